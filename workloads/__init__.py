@@ -1,0 +1,219 @@
+"""Seeded synthetic workloads for the parametrized diffusion problems.
+
+This module only *describes* problems and *draws* random numbers.  It holds
+none of the method's arithmetic (no operator, no solver, no projection), so
+both the FP64 oracle and the CUDA library can take their inputs from it
+without sharing any computation.
+
+Problem family (the paper's eq. 1 with the affine form of eq. 12):
+    -div(kappa(x; mu) grad u) = f(x; mu) on the unit square / cube,
+    u = 0 on the boundary, kappa = mu_p on block p of a box partition,
+    f = sum_r phi_r(mu) f_r.
+The grid, block partition and load terms of each workload are plain data
+here; the discretisation itself is written independently in `oracle/` and in
+the CUDA kernels.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood 2014, "Fast
+splittable pseudorandom number generators"): state += 0x9E3779B97F4A7C15,
+then two xor-shift-multiply rounds.  A double in [0, 1) is (z >> 11) * 2^-53.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+_GOLDEN = 0x9E3779B97F4A7C15
+_M1 = 0xBF58476D1CE4E5B9
+_M2 = 0x94D049BB133111EB
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """`count` consecutive SplitMix64 outputs of the stream that starts at `seed`."""
+    out = np.empty(count, dtype=np.uint64)
+    s = seed & _MASK
+    for i in range(count):
+        s = (s + _GOLDEN) & _MASK
+        z = s
+        z = ((z ^ (z >> 30)) * _M1) & _MASK
+        z = ((z ^ (z >> 27)) * _M2) & _MASK
+        out[i] = z ^ (z >> 31)
+    return out
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """Doubles in [0, 1): the top 53 bits of each SplitMix64 output times 2^-53."""
+    z = splitmix64(seed, count)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+@dataclasses.dataclass(frozen=True)
+class Load:
+    """One load term f_r of f(mu) = sum_r phi_r(mu) f_r.
+
+    kind  : "const" (f_r = 1 at every node) or "gauss"
+            (f_r(x) = exp(-|x - center|^2 / (2 sigma^2)) at node coordinates).
+    param : -1 means phi_r = 1; otherwise phi_r = mu[param].
+    """
+    kind: str
+    param: int = -1
+    center: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    sigma: float = 0.0
+
+
+@dataclasses.dataclass(frozen=True)
+class Problem:
+    """Grid, block partition and load terms of one parametrized diffusion problem.
+
+    dims   : interior nodes per direction, (mx, my) or (mx, my, mz); x fastest.
+    blocks : blocks per direction; P = prod(blocks) diffusion parameters.
+    loads  : load terms; mu has P + n_load_params entries.
+    """
+    dims: Tuple[int, ...]
+    blocks: Tuple[int, ...]
+    loads: Tuple[Load, ...]
+
+    @property
+    def dim(self) -> int:
+        return len(self.dims)
+
+    @property
+    def n_dof(self) -> int:
+        return int(np.prod(self.dims))
+
+    @property
+    def P(self) -> int:
+        return int(np.prod(self.blocks))
+
+    @property
+    def n_mu(self) -> int:
+        extra = [ld.param for ld in self.loads if ld.param >= 0]
+        return max([self.P - 1] + extra) + 1
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named workload: problem, basis size and the seeded parameter sets."""
+    name: str
+    problem: Problem
+    n_basis: int
+    mu_range: Tuple[float, float]          # log-uniform range of the P block values
+    load_range: Tuple[float, float]        # uniform range of the load parameters
+    n_train: int
+    n_test: int
+    batch: int
+    train_seed: int = 1
+    test_seed: int = 2
+    bump_seed: int = 3
+
+    def draw_mu(self, seed: int, count: int) -> np.ndarray:
+        """count x n_mu parameter vectors from stream `seed`.
+
+        Each vector draws n_mu uniforms in order; the first P become
+        exp(ln a + u (ln b - ln a)) (log-uniform block values), the rest
+        lo + u (hi - lo) (load parameters).
+        """
+        P, n_mu = self.problem.P, self.problem.n_mu
+        u = uniform01(seed, count * n_mu).reshape(count, n_mu)
+        a, b = self.mu_range
+        mu = np.empty_like(u)
+        mu[:, :P] = np.exp(math.log(a) + u[:, :P] * (math.log(b) - math.log(a)))
+        lo, hi = self.load_range
+        mu[:, P:] = lo + u[:, P:] * (hi - lo)
+        return mu
+
+    def train_mu(self) -> np.ndarray:
+        return self.draw_mu(self.train_seed, self.n_train)
+
+    def test_mu(self, count: int | None = None) -> np.ndarray:
+        return self.draw_mu(self.test_seed, self.n_test if count is None else count)
+
+
+def bump_centers(seed: int, count: int, dim: int, lo: float = 0.2, hi: float = 0.8) -> np.ndarray:
+    """count x dim Gaussian-bump centres, uniform in [lo, hi]^dim."""
+    u = uniform01(seed, count * dim).reshape(count, dim)
+    return lo + u * (hi - lo)
+
+
+def _const_load() -> Tuple[Load, ...]:
+    return (Load("const"),)
+
+
+def _bump_loads(seed: int, dim: int, P: int, sigma: float = 0.05) -> Tuple[Load, ...]:
+    c = bump_centers(seed, 2, dim)
+    pad = lambda v: tuple(float(t) for t in v) + (0.0,) * (3 - dim)
+    return (Load("const"),
+            Load("gauss", param=P + 0, center=pad(c[0]), sigma=sigma),
+            Load("gauss", param=P + 1, center=pad(c[1]), sigma=sigma))
+
+
+def rbi_2d_64() -> Workload:
+    """2D, 64x64 interior grid, 2x2 blocks, f = 1, n = 20, 200 train / 50 test."""
+    prob = Problem(dims=(64, 64), blocks=(2, 2), loads=_const_load())
+    return Workload("rbi_2d_64x64_P4_n20", prob, n_basis=20, mu_range=(0.1, 10.0),
+                    load_range=(0.0, 1.0), n_train=200, n_test=50, batch=50)
+
+
+def rbcg_2d_512() -> Workload:
+    """2D, 512x512 interior grid, 3x3 blocks, f = 1 + mu_9 f_1 + mu_10 f_2, n = 40."""
+    P = 9
+    prob = Problem(dims=(512, 512), blocks=(3, 3), loads=_bump_loads(3, 2, P))
+    return Workload("rbcg_2d_512x512_P9_n40", prob, n_basis=40, mu_range=(0.1, 10.0),
+                    load_range=(0.0, 1.0), n_train=1000, n_test=1000, batch=1000)
+
+
+def batched_3d_128() -> Workload:
+    """3D, 128^3 interior grid, 2x2x2 blocks, f = 1, n = 60, 256 queries per launch."""
+    prob = Problem(dims=(128, 128, 128), blocks=(2, 2, 2), loads=_const_load())
+    return Workload("rbcg_3d_128cube_P8_n60", prob, n_basis=60, mu_range=(0.1, 10.0),
+                    load_range=(0.0, 1.0), n_train=512, n_test=256, batch=256)
+
+
+def ragged_3d(m: int) -> Workload:
+    """3D m^3 member of the ragged batch (m in 64, 96, 128), 2x2x2 blocks, n = 60."""
+    prob = Problem(dims=(m, m, m), blocks=(2, 2, 2), loads=_const_load())
+    return Workload(f"rbcg_3d_{m}cube_P8_n60", prob, n_basis=60, mu_range=(0.1, 10.0),
+                    load_range=(0.0, 1.0), n_train=512, n_test=256, batch=256)
+
+
+def large_3d_256() -> Workload:
+    """3D, 256^3 interior grid, 3x3x3 blocks, mu in [0.01, 100], f = 1, n = 100."""
+    prob = Problem(dims=(256, 256, 256), blocks=(3, 3, 3), loads=_const_load())
+    return Workload("rbcg_3d_256cube_P27_n100", prob, n_basis=100, mu_range=(0.01, 100.0),
+                    load_range=(0.0, 1.0), n_train=512, n_test=64, batch=64)
+
+
+def small(dims: Sequence[int], blocks: Sequence[int], n_basis: int, n_train: int = 40,
+          bumps: bool = False, mu_range=(0.1, 10.0), name: str | None = None) -> Workload:
+    """A small problem of the same family, for tests that must finish in seconds."""
+    dims, blocks = tuple(dims), tuple(blocks)
+    P = int(np.prod(blocks))
+    loads = _bump_loads(3, len(dims), P) if bumps else _const_load()
+    prob = Problem(dims=dims, blocks=blocks, loads=loads)
+    nm = name or ("small_" + "x".join(map(str, dims)) + "_P%d_n%d" % (P, n_basis))
+    return Workload(nm, prob, n_basis=n_basis, mu_range=mu_range, load_range=(0.0, 1.0),
+                    n_train=n_train, n_test=16, batch=16)
+
+
+WORKLOADS = {
+    "rbi_2d_64": rbi_2d_64,
+    "rbcg_2d_512": rbcg_2d_512,
+    "batched_3d_128": batched_3d_128,
+    "large_3d_256": large_3d_256,
+}
+
+
+def load_arrays(problem: Problem):
+    """Flatten the load descriptors to arrays (kind code, param, centre, sigma).
+
+    kind code: 0 = const, 1 = gauss.  This is a format conversion for the
+    C interface, not arithmetic of the method.
+    """
+    kinds = np.array([0 if ld.kind == "const" else 1 for ld in problem.loads], dtype=np.int32)
+    params = np.array([ld.param for ld in problem.loads], dtype=np.int32)
+    centers = np.array([ld.center for ld in problem.loads], dtype=np.float64).reshape(-1, 3)
+    sigmas = np.array([ld.sigma for ld in problem.loads], dtype=np.float64)
+    return kinds, params, centers, sigmas
