@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: RB-preconditioned CG (Alg. 3) solves per second on one or more GB300s.
+
+One step = one batch of test queries solved to true relative residual 1e-10
+(the whole online hot path: reduced set-up, FP64 residual refinement, FP32
+inner RBCG with RBI preconditioner, tensor-core projections), inputs resident
+in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RB-PCG solves/sec to rel. residual 1e-10 (mixed+batched vs FP64 plain), % HBM roofline"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
+
+# Algorithmic bytes per grid point per launch unit (one query, one pass), by kernel
+# and inner precision: every operand read or written once (eq. 5-8 and Alg. 3 steps).
+BYTES_PER_POINT = {
+    "f32": {"cg_a": 12, "cg_b": 20, "smooth": 16, "project": 4, "tc_project": 4, "prolong": 4, "tc_prolong": 4,
+            "outer_residual": 12, "outer_update": 24},
+    "f64": {"cg_a": 24, "cg_b": 40, "smooth": 32, "project": 8, "prolong": 8, "outer_residual": 16},
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rbcg_2d_512")
+    ap.add_argument("--batch", type=int, default=0, help="queries per step and GPU (default: the workload's)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nu", type=int, default=1)
+    ap.add_argument("--gemm", default="auto")
+    ap.add_argument("--fp64-queries", type=int, default=256, help="queries of the FP64 plain comparator (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=40, help="Alg. 3 iterations per core in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q, "--format=csv",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.strip() for ln in open(self.f.name) if ln.strip() and not ln.startswith("index")]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            c = [t.strip() for t in r.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1].split()[0]))
+                smax.append(float(c[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def load_golden():
+    if os.path.exists(GOLDEN):
+        return json.load(open(GOLDEN))
+    return None
+
+
+def cpu_sample(workload_name, n_cores, iters_per_core, steps=1):
+    """Time the oracle's Alg. 3 on the host cores; returns a cpu_baseline-style dict."""
+    import workloads as wl
+    from oracle import baseline
+    g = load_golden()
+    if g is None or g.get("workload") != wl.WORKLOADS[workload_name]().name:
+        return None, "no stored oracle greedy selection for this workload"
+    runner = baseline.OracleRunner(workload_name, g["selected"], n_cores)
+    w = wl.WORKLOADS[workload_name]()
+    mu = w.test_mu(n_cores * max(1, steps))
+    mean_iters = float(sum(g["iters"])) / len(g["iters"])
+    out = []
+    for s in range(steps):
+        its, wall = runner.sample(mu[s * n_cores:(s + 1) * n_cores], iters_per_core)
+        out.append((its, wall))
+    runner.close()
+    return {"mean_iters_per_solve": mean_iters, "samples": out, "setup_s": runner.setup_s}, None
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle (Alg. 3) timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as wl
+    w = wl.WORKLOADS[args.workload]()
+    cores = min(16, os.cpu_count() or 1)
+    res, why = cpu_sample(args.workload, cores, args.cpu_iters, steps=args.warmup + args.steps)
+    if res is None:
+        print(json.dumps({"impl": "reference", "unavailable": why}))
+        return
+    timed = res["samples"][args.warmup:]
+    its = sum(t[0] for t in timed)
+    wall = sum(t[1] for t in timed)
+    value = its / wall / res["mean_iters_per_solve"]
+    sample = (f"{cores} test parameters per step, one per core, {args.cpu_iters} Alg. 3 iterations each; "
+              f"solves/s = iteration rate / the oracle's mean {res['mean_iters_per_solve']:.1f} iterations per "
+              f"solve (tests/golden/rbcg_2d_512_oracle.json)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, len(timed)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "solver": "oracle FP64 Alg. 3 (numpy)",
+                                            "cores": cores},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = wl.WORKLOADS[args.workload]()
+    prob = w.problem
+    B = args.batch or w.batch
+    N = prob.n_dof
+
+    # ---- offline (not timed): greedy basis on the GPU
+    t0 = time.perf_counter()
+    ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B)
+    offline_s = time.perf_counter() - t0
+    _, _, _, _, sel = ctx.basis()
+
+    # weak scaling: every rank solves its own B test parameters
+    mu_all = w.test_mu(B * world) if B * world <= w.n_test else w.draw_mu(w.test_seed, B * world)
+    mu = np.ascontiguousarray(mu_all[rank * B:(rank + 1) * B])
+    x = torch.zeros((B, N), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, stream=stream.cuda_stream)
+
+    def step(xbuf, **kw):
+        status, st = ctx.pcg(mu, xbuf, **{**opts, **kw})
+        return status, st
+
+    for _ in range(args.warmup):
+        status, st = step(x)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        status, st = step(x)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_local = e0.elapsed_time(e1) / 1000.0
+    if world > 1:
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    else:
+        t_max = t_local
+    value = world * B * args.steps / t_max
+    last = stats[-1]
+    ok = bool(np.all(last["status"] == rb.RB_OK))
+
+    # ---- per-kernel device time (CUDA events around every launch; separate pass)
+    ctx.profile(True)
+    _, st_prof = step(x)
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    torch.cuda.synchronize()
+    launches_per_step = sum(v[0] for v in prof.values())
+    prec = "f32" if args.precision == "mixed" else "f64"
+    iters = int(st_prof["iters"].sum())
+    outers = int(st_prof["outer"].sum())
+    units = {"cg_a": iters, "cg_b": iters, "smooth": iters * max(1, args.nu), "project": iters,
+             "tc_project": iters, "prolong": iters, "tc_prolong": iters, "outer_residual": outers,
+             "outer_update": outers}
+    kernels = {}
+    for k, (n_launch, ms) in prof.items():
+        bpp = BYTES_PER_POINT[prec].get(k)
+        entry = {"launches": n_launch, "ms": round(ms, 3)}
+        if bpp is not None and ms > 0:
+            alg = bpp * N * units[k]
+            entry["alg_bytes"] = alg
+            entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
+        kernels[k] = entry
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    peak, peak_kind = measured_peaks()
+    achieved = kernels[dom].get("gbs")
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                "peak_source": peak_kind,
+                "alg_bytes_per_unit": BYTES_PER_POINT[prec].get(dom),
+                "unit_def": "one query x one grid point per launch"}
+
+    # ---- end to end through the C interface with host buffers (pinned)
+    xh = torch.zeros((B, N), dtype=torch.float64, pin_memory=True).numpy()
+    ctx.pcg(mu, xh, **{**opts, "stream": stream.cuda_stream})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.pcg(mu, xh, **opts)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * B * args.steps / e2e_s if world == 1 else None, "unit": "solves/s",
+           "h2d_bytes_per_step": int(mu.nbytes), "d2h_bytes_per_step": int(B * N * 8 + B * 24)}
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * B * args.steps / float(t.item())
+
+    # ---- FP64 plain comparator (same GPU, same workload, fewer queries)
+    fp64 = None
+    if args.fp64_queries > 0 and args.precision == "mixed":
+        q64 = min(B, args.fp64_queries)
+        x64 = torch.zeros((q64, N), dtype=torch.float64, device=dev)
+        ctx.pcg(mu[:q64], x64, **{**opts, "precision": "fp64"})
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st64 = ctx.pcg(mu[:q64], x64, **{**opts, "precision": "fp64"})
+        b.record(stream)
+        torch.cuda.synchronize()
+        s64 = a.elapsed_time(b) / 1000.0
+        fp64 = {"value": q64 / s64, "unit": "solves/s", "queries": q64,
+                "mean_iters": float(st64["iters"].mean()), "all_converged": bool(np.all(st64["status"] == 0)),
+                "max_rel_res": float(st64["rel_res"].max())}
+
+    # ---- CPU baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = min(16, os.cpu_count() or 1)
+        try:
+            res, why = cpu_sample(args.workload, cores, args.cpu_iters, steps=1)
+        except Exception as e:  # the baseline must not sink the GPU number
+            res, why = None, f"oracle sample failed: {e}"
+        if res is not None:
+            its, wall = res["samples"][0]
+            cpu = {"value": its / wall / res["mean_iters_per_solve"], "unit": "solves/s", "cores": cores,
+                   "kind": "oracle",
+                   "sample": (f"{cores} test parameters, one per core, {args.cpu_iters} iterations of the oracle's "
+                              f"FP64 Alg. 3 each ({its} in {wall:.1f} s); solves/s = iteration rate / the oracle's "
+                              f"mean {res['mean_iters_per_solve']:.1f} iterations per solve")}
+        else:
+            cpu = {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": why}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": "x".join(map(str, prob.dims)), "P": prob.P, "n_basis": w.n_basis,
+                       "queries_per_step_per_gpu": B, "precision": args.precision, "beta": "pr",
+                       "smoother": f"red-black GS nu={args.nu}", "tol": 1e-10, "gemm": args.gemm,
+                       "l2": "inputs larger than L2 (FP64 solutions %.1f GB + FP32 work vectors per step)"
+                             % (B * N * 8 / 1e9),
+                       "offline_build_s": round(offline_s, 1), "greedy_selected_first": [int(s) for s in sel[:8]]},
+            "all_converged": ok, "mean_iters": float(last["iters"].mean()), "max_iters": int(last["iters"].max()),
+            "mean_outer": float(last["outer"].mean()), "max_rel_res": float(last["rel_res"].max()),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
+            "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * rb.h - C interface of librb: the online phase of the reduced-basis (RB)
+ * iteration (Alg. 2) and RB-preconditioned conjugate gradients (Alg. 3) for
+ * many-query parametrized SPD systems A(mu) x = f(mu) (eq. 1) with the affine
+ * form A(mu) = sum_q Theta_q(mu) A_q, f(mu) = sum_r Phi_r(mu) f_r (eq. 12).
+ *
+ * Problem family.  -div(kappa grad u) = f on the unit square / cube with
+ * u = 0 on the boundary, discretised by finite differences on m_d interior
+ * nodes per direction (h_d = 1/(m_d+1), x fastest).  kappa = mu_p on block p
+ * of a box partition, block of node i_d is floor(i_d * nb_d / m_d); a face
+ * between two nodes carries (mu_p(i) + mu_p(j))/2, a face to the boundary
+ * mu_p(i).  Theta_q(mu) = mu_q, Q = P = nb_x nb_y nb_z.
+ *
+ * Conventions for every call:
+ *  - Vectors of a batch are [B][N_dof] doubles, query-major, x fastest.
+ *  - Pointers named "host or device" may point to either; the library asks
+ *    the CUDA runtime which one it is.  Host buffers are copied in and out
+ *    inside the call.  Device buffers must be allocated on the current device.
+ *  - Parameter vectors mu are always host memory, [B][n_mu] doubles.
+ *  - Calls are ordered on opts->stream (NULL = legacy default stream) and are
+ *    synchronous: they return after the per-query statistics are on the host.
+ *  - A context is not reentrant: one call at a time per rb_ctx.
+ *  - Errors: every call returns an rb_status; rb_last_error() gives the text
+ *    of the last failure on that context.  Per-query outcomes go to
+ *    stats[i].status; the call returns the worst of them.
+ */
+#ifndef RB_H
+#define RB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rb_ctx rb_ctx;
+
+typedef enum {
+    RB_OK = 0,
+    RB_EINVAL = 1,      /* bad argument (dimensions, null pointer, non-finite mu) */
+    RB_ENOMEM = 2,      /* device or host allocation failed */
+    RB_EFORMAT = 3,     /* malformed or corrupted basis file */
+    RB_ECUDA = 4,       /* a CUDA runtime call failed */
+    RB_EBREAKDOWN = 5,  /* non-positive Cholesky pivot, p^T A p <= 0 or NaN */
+    RB_ENOCONV = 6,     /* iteration budget spent before the tolerance was met */
+    RB_ETIMEOUT = 7,    /* a device-side wait gave up */
+    RB_EIO = 8          /* file could not be opened, read or written */
+} rb_status;
+
+/* One load term f_r of f(mu) = sum_r Phi_r(mu) f_r (eq. 12). */
+enum { RB_LOAD_CONST = 0, RB_LOAD_GAUSS = 1 };
+typedef struct {
+    int kind;           /* RB_LOAD_CONST: f_r = 1; RB_LOAD_GAUSS: exp(-|x-c|^2/(2 sigma^2)) */
+    int param;          /* -1: Phi_r = 1; otherwise Phi_r(mu) = mu[param] */
+    double center[3];
+    double sigma;
+} rb_load;
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int m[3];           /* interior nodes per direction; m[2] = 1 when dim = 2 */
+    int nb[3];          /* blocks per direction; nb[2] = 1 when dim = 2 */
+    int n_loads;        /* R >= 1 */
+    const rb_load* loads;
+    int n_mu;           /* entries of one parameter vector (>= P and > every load param) */
+} rb_problem;
+
+enum { RB_SMOOTH_NONE = 0, RB_SMOOTH_RBGS = 1, RB_SMOOTH_JACOBI = 2 };
+enum { RB_PREC_FP64 = 0, RB_PREC_MIXED = 1 };
+enum { RB_BETA_FR = 0, RB_BETA_PR = 1 };
+enum { RB_X0_ZERO = 0, RB_X0_GIVEN = 1 };
+enum { RB_GEMM_AUTO = 0, RB_GEMM_CUDA_CORES = 1, RB_GEMM_TENSOR = 2 };
+
+typedef struct {
+    double tol;         /* stop at ||f - A x|| / ||f|| < tol (true FP64 residual) */
+    int max_iter;       /* iteration budget per query */
+    int smoother;       /* RB_SMOOTH_*: S(A, b, y) of eq. 8 */
+    int nu;             /* smoother sweeps per application */
+    double omega;       /* Jacobi weight */
+    int precision;      /* RB_PREC_FP64: all FP64; RB_PREC_MIXED: FP32 inner RBCG
+                           with FP64 residual refinement (rb_pcg only) */
+    int beta_form;      /* RB_BETA_FR (Alg. 3 as printed) or RB_BETA_PR */
+    int x0_mode;        /* RB_X0_ZERO or RB_X0_GIVEN (x holds the start on entry) */
+    double inner_tol;   /* mixed: relative residual reduction of each FP32 solve */
+    int max_outer;      /* mixed: maximum FP64 refinement steps */
+    int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
+    int graph;          /* 1: replay the iteration body as a captured CUDA graph */
+    void* stream;       /* cudaStream_t or NULL */
+} rb_opts;
+
+typedef struct {
+    int iters;          /* RBI: corrections applied; RBCG: matrix-vector products (inner ones in mixed mode) */
+    int outer;          /* FP64 residual evaluations (refinement steps + final check) */
+    int restarts;       /* residual replacements after a failed true-residual check */
+    int status;         /* rb_status of this query */
+    double rel_res;     /* final true ||f - A x|| / ||f|| in FP64 */
+} rb_stats;
+
+typedef struct {
+    double truth_tol;   /* relative residual of the snapshot solves (default 1e-11) */
+    int truth_max_iter; /* budget of one snapshot solve (default 200000) */
+    int score;          /* 0: L1 norm of the coefficients in the snapshot basis; 1: literal RB coefficients */
+    double drop_tol;    /* a snapshot whose Gram-Schmidt remainder is below drop_tol ||x|| is skipped */
+} rb_build_opts;
+
+/* Fill defaults: tol 1e-10, red-black Gauss-Seidel with nu = 1, FP64, PR beta,
+ * zero start, inner_tol 1e-5, max_outer 12, automatic GEMM engine, graphs on. */
+void rb_default_opts(rb_opts* opts);
+void rb_default_build_opts(rb_build_opts* opts);
+
+/*
+ * Online context from precomputed offline arrays (Section 2.3, eq. 12c).
+ *   W   host, [N_dof][n] row-major: the orthonormal basis W_N;
+ *   ANq host, [Q][n][n]: A_{N,q} = W^T A_q W;  fNr host, [R][n]: f_{N,r} = W^T f_r.
+ *   n may be 0 (no basis: the RB correction is skipped).
+ * max_batch fixes the device workspace: larger batches are run in waves.
+ * All device memory of the context is allocated here; solves allocate nothing.
+ * On failure *out is NULL and nothing is leaked.
+ */
+rb_status rb_offline_load_arrays(rb_ctx** out, const rb_problem* prob, int n,
+                                 const double* W, const double* ANq, const double* fNr,
+                                 int max_batch);
+
+/* Offline greedy (Alg. 1 steps, snapshots solved on the device by RBCG with
+ * W_{N-1} as in Alg. 4; Gram-Schmidt twice; eq. 12c grown one row and column
+ * per step).  mu_train host [n_train][n_mu]; the first training vector is mu_1.
+ * Produces a context with n = n_max basis vectors (fewer if the training set
+ * runs out of independent snapshots). */
+rb_status rb_offline_build(rb_ctx** out, const rb_problem* prob, int n_max, int n_train,
+                           const double* mu_train, const rb_build_opts* bopts,
+                           const rb_opts* solve_opts, int max_batch);
+
+/* Basis file (.rbb): header, W, A_{N,q}, f_{N,r}, snapshot factor R,
+ * selected training indices, FNV-1a checksum.  Load fails with RB_EFORMAT on a
+ * bad magic, size or checksum and RB_EIO when the file cannot be read. */
+rb_status rb_save(const rb_ctx* ctx, const char* path);
+rb_status rb_offline_load(rb_ctx** out, const char* path, int max_batch);
+
+/* Sizes of a context: N_dof, basis size n, Q (= P), R, n_mu. Any pointer may be NULL. */
+rb_status rb_info(const rb_ctx* ctx, long long* n_dof, int* n, int* Q, int* R, int* n_mu);
+
+/* Copy the offline data back to host arrays laid out as in
+ * rb_offline_load_arrays; Rsnap [n][n] (upper, X = W R; zero if unknown),
+ * selected [n] (-1 if unknown).  Any pointer may be NULL. */
+rb_status rb_get_basis(const rb_ctx* ctx, double* W, double* ANq, double* fNr,
+                       double* Rsnap, int* selected);
+
+/*
+ * RB iteration, Alg. 2: x <- 0; repeat r = f - A x (stop when ||r|| < tol ||f||),
+ * r_N = W^T r (eq. 5), A_N e_N = r_N (eq. 6, Cholesky), x += W e_N (eq. 7),
+ * x = S(A, f, x) (eq. 8).  FP64 throughout.
+ *   mu host [B][n_mu];  x host or device [B][N_dof], written with the solutions
+ *   (read first when opts->x0_mode == RB_X0_GIVEN);  stats host [B] or NULL.
+ */
+rb_status rb_solve(rb_ctx* ctx, int B, const double* mu, double* x,
+                   const rb_opts* opts, rb_stats* stats);
+
+/*
+ * RB-preconditioned CG, Alg. 3, preconditioner y = RBI(A, r, W, 1) from zero:
+ * y = W A_N^{-1} W^T r then S(A, r, y).  opts->precision selects plain FP64 or
+ * the mixed scheme (FP32 inner RBCG, TF32/FP32 projections, FP64 residual and
+ * solution, iterative refinement to opts->tol).  Arguments as rb_solve.
+ */
+rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x,
+                 const rb_opts* opts, rb_stats* stats);
+
+/* y = A(mu_b) x_b for every query b (eq. 1 operator, FP64).  x, y host or device
+ * [B][N_dof]; stream as in rb_opts (may be NULL). */
+rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y,
+                   void* stream);
+
+/* Per-kernel timing.  rb_profile(ctx, 1) clears the counters and from then on
+ * brackets every kernel launch of rb_solve / rb_pcg with CUDA events on the
+ * call's stream (the iteration body is then launched directly, not as a CUDA
+ * graph); rb_profile(ctx, 0) stops.  rb_profile_read copies up to cap entries
+ * (one per kernel kind that ran: launches and summed device milliseconds) and
+ * sets *count to the number of kinds. */
+typedef struct {
+    char name[24];
+    long long launches;
+    double ms;
+} rb_kernel_time;
+rb_status rb_profile(rb_ctx* ctx, int enable);
+rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* count);
+
+/* Text of the last error on ctx (or of the last failed context creation when
+ * ctx is NULL).  Valid until the next call on that context. */
+const char* rb_last_error(const rb_ctx* ctx);
+const char* rb_status_string(rb_status s);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void rb_free(rb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB_H */

@@ -1,0 +1,784 @@
+// C interface of librb (include/rb.h): context set-up, the batched solve
+// drivers, the offline greedy and the basis file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rb_common.cuh"
+#include "rb_tc.cuh"
+
+using namespace rbk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+};
+
+}  // namespace
+
+struct rb_ctx {
+    // problem
+    int dim = 2, m[3] = {1, 1, 1}, nbk[3] = {1, 1, 1}, P = 1, R = 1, n_mu = 1;
+    long long N = 0;
+    std::vector<rb_load> loads;
+    int load_param[MAX_LOADS] = {0};
+    Geo geo{};
+    int *d_bx = nullptr, *d_by = nullptr, *d_bz = nullptr;
+    double* d_fr = nullptr;
+    // basis
+    int n = 0, n_cap = 0, nbp = 16, nbp32 = 32;
+    double* d_W64c = nullptr;
+    float* d_W32c = nullptr;
+    float* d_W32r = nullptr;
+    double* d_ANq = nullptr;
+    double* d_fNr = nullptr;
+    std::vector<double> h_ANq, h_fNr, h_Rsnap;
+    std::vector<int> selected;
+    // workspace
+    int Bmax = 1;
+    double* d_x64 = nullptr;
+    double *d_r64 = nullptr, *d_p64 = nullptr, *d_y64 = nullptr, *d_ypro64 = nullptr, *d_tmp64 = nullptr;
+    float *d_r32 = nullptr, *d_p32 = nullptr, *d_y32 = nullptr, *d_ypro32 = nullptr, *d_tmp32 = nullptr,
+          *d_d32 = nullptr;
+    double* d_e64 = nullptr;
+    float* d_e32 = nullptr;
+    double* d_L = nullptr;
+    double* d_mu = nullptr;
+    QState* d_st = nullptr;
+    double* d_part = nullptr;
+    int max_tiles = 1;
+    double* d_proj = nullptr;
+    int nsplit = 1;
+    unsigned* d_tick = nullptr;
+    int* d_lcnt = nullptr;
+    int* d_lidx = nullptr;
+    int* d_ndone = nullptr;
+    double* d_scratch = nullptr;      // offline helpers
+    size_t scratch_bytes = 0;
+    TcPlan tc{};                      // tensor-core projection plans
+    bool force_generic = false;       // testing: use the generic stencil kernels everywhere
+    // per-kernel timing (rb_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> prof_pending;   // (kernel kind, first event index)
+    double prof_ms[32] = {0};
+    long long prof_launches[32] = {0};
+    // host
+    QState* h_st = nullptr;
+    int* h_ndone = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int num_sms = 1;
+    int grid = 1;
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+            return RB_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+template <typename T>
+rb_status dalloc(rb_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e);
+        *p = nullptr;
+        return RB_ENOMEM;
+    }
+    ctx->allocs.push_back((void*)*p);
+    return RB_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        rb_status s_ = (x);           \
+        if (s_ != RB_OK) return s_;   \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pad_to(int v, int m) { return ((v + m - 1) / m) * m; }
+
+rb_status validate_problem(const rb_problem* prob, std::string& why) {
+    if (!prob) { why = "problem is NULL"; return RB_EINVAL; }
+    if (prob->dim != 2 && prob->dim != 3) { why = "dim must be 2 or 3"; return RB_EINVAL; }
+    long long P = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (prob->m[d] < 1 || prob->nb[d] < 1 || prob->nb[d] > prob->m[d]) {
+            why = "grid sizes must be >= 1 and blocks must lie in 1..m per direction";
+            return RB_EINVAL;
+        }
+        P *= prob->nb[d];
+    }
+    if (prob->dim == 2 && (prob->m[2] != 1 || prob->nb[2] != 1)) { why = "dim 2 needs m[2] = nb[2] = 1"; return RB_EINVAL; }
+    if (P > MAX_P) { why = "too many blocks (max 64)"; return RB_EINVAL; }
+    if ((long long)prob->m[0] * prob->m[1] * prob->m[2] >= (1LL << 31)) { why = "grid too large (N_dof >= 2^31)"; return RB_EINVAL; }
+    if (prob->n_loads < 1 || prob->n_loads > MAX_LOADS || !prob->loads) { why = "need 1..8 load terms"; return RB_EINVAL; }
+    if (prob->n_mu < P || prob->n_mu > MAX_MU) { why = "n_mu must be in P..128"; return RB_EINVAL; }
+    for (int r = 0; r < prob->n_loads; ++r) {
+        const rb_load& l = prob->loads[r];
+        if (l.kind != RB_LOAD_CONST && l.kind != RB_LOAD_GAUSS) { why = "unknown load kind"; return RB_EINVAL; }
+        if (l.param >= prob->n_mu || l.param < -1) { why = "load parameter index out of range"; return RB_EINVAL; }
+        if (l.kind == RB_LOAD_GAUSS && !(l.sigma > 0.0)) { why = "Gaussian load needs sigma > 0"; return RB_EINVAL; }
+    }
+    return RB_OK;
+}
+
+// Allocate everything of a context for basis capacity n_cap and batch Bmax.
+rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch) {
+    ctx->dim = prob->dim;
+    for (int d = 0; d < 3; ++d) { ctx->m[d] = prob->m[d]; ctx->nbk[d] = prob->nb[d]; }
+    ctx->P = prob->nb[0] * prob->nb[1] * prob->nb[2];
+    ctx->R = prob->n_loads;
+    ctx->n_mu = prob->n_mu;
+    ctx->N = (long long)prob->m[0] * prob->m[1] * prob->m[2];
+    ctx->loads.assign(prob->loads, prob->loads + prob->n_loads);
+    for (int r = 0; r < ctx->R; ++r) ctx->load_param[r] = prob->loads[r].param;
+    ctx->n_cap = n_cap;
+    ctx->nbp = std::max(16, pad_to(n_cap, 16));
+    ctx->nbp32 = std::max(32, pad_to(n_cap, 32));
+    ctx->Bmax = max_batch;
+    const long long N = ctx->N;
+    const int B = max_batch;
+
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    ctx->grid = ctx->num_sms * 8;
+    CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamDefault));
+
+    // geometry and block maps
+    std::vector<int> maps[3];
+    for (int d = 0; d < 3; ++d) {
+        maps[d].resize(ctx->m[d]);
+        for (int i = 0; i < ctx->m[d]; ++i) maps[d][i] = (int)(((long long)i * ctx->nbk[d]) / ctx->m[d]);
+    }
+    TRY(dalloc(ctx, &ctx->d_bx, ctx->m[0]));
+    TRY(dalloc(ctx, &ctx->d_by, ctx->m[1]));
+    TRY(dalloc(ctx, &ctx->d_bz, ctx->m[2]));
+    CK(cudaMemcpy(ctx->d_bx, maps[0].data(), ctx->m[0] * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_by, maps[1].data(), ctx->m[1] * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bz, maps[2].data(), ctx->m[2] * sizeof(int), cudaMemcpyHostToDevice));
+    Geo& g = ctx->geo;
+    g.dim = ctx->dim;
+    g.mx = ctx->m[0]; g.my = ctx->m[1]; g.mz = ctx->m[2];
+    g.nbx = ctx->nbk[0]; g.nby = ctx->nbk[1]; g.nbz = ctx->nbk[2];
+    g.P = ctx->P;
+    g.n = N;
+    g.ihx2 = (double)(g.mx + 1) * (g.mx + 1);
+    g.ihy2 = (double)(g.my + 1) * (g.my + 1);
+    g.ihz2 = ctx->dim == 3 ? (double)(g.mz + 1) * (g.mz + 1) : 0.0;
+    g.bx = ctx->d_bx; g.by = ctx->d_by; g.bz = ctx->d_bz;
+
+    // load terms
+    TRY(dalloc(ctx, &ctx->d_fr, (size_t)ctx->R * N));
+    {
+        std::vector<int> kind(ctx->R);
+        std::vector<double> center(3 * ctx->R), sigma(ctx->R);
+        for (int r = 0; r < ctx->R; ++r) {
+            kind[r] = ctx->loads[r].kind;
+            for (int j = 0; j < 3; ++j) center[3 * r + j] = ctx->loads[r].center[j];
+            sigma[r] = ctx->loads[r].sigma;
+        }
+        int* dk; double *dc, *ds;
+        TRY(dalloc(ctx, &dk, ctx->R));
+        TRY(dalloc(ctx, &dc, 3 * ctx->R));
+        TRY(dalloc(ctx, &ds, ctx->R));
+        CK(cudaMemcpy(dk, kind.data(), ctx->R * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dc, center.data(), 3 * ctx->R * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ds, sigma.data(), ctx->R * sizeof(double), cudaMemcpyHostToDevice));
+        launch_fill_loads(g, ctx->R, dk, dc, ds, ctx->d_fr, ctx->own_stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->own_stream));
+    }
+
+    // basis storage
+    const int nbp = ctx->nbp;
+    TRY(dalloc(ctx, &ctx->d_W64c, (size_t)nbp * N));
+    TRY(dalloc(ctx, &ctx->d_W32c, (size_t)nbp * N));
+    TRY(dalloc(ctx, &ctx->d_W32r, (size_t)ctx->nbp32 * N));
+    CK(cudaMemset(ctx->d_W64c, 0, (size_t)nbp * N * sizeof(double)));
+    CK(cudaMemset(ctx->d_W32c, 0, (size_t)nbp * N * sizeof(float)));
+    CK(cudaMemset(ctx->d_W32r, 0, (size_t)ctx->nbp32 * N * sizeof(float)));
+    TRY(dalloc(ctx, &ctx->d_ANq, (size_t)ctx->P * std::max(1, n_cap) * std::max(1, n_cap)));
+    TRY(dalloc(ctx, &ctx->d_fNr, (size_t)ctx->R * std::max(1, n_cap)));
+
+    // batch workspace
+    const size_t BN = (size_t)B * N;
+    TRY(dalloc(ctx, &ctx->d_x64, BN));
+    TRY(dalloc(ctx, &ctx->d_r64, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_p64, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_y64, BN));
+    TRY(dalloc(ctx, &ctx->d_ypro64, BN));
+    TRY(dalloc(ctx, &ctx->d_tmp64, BN));
+    TRY(dalloc(ctx, &ctx->d_r32, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_p32, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_y32, BN));
+    TRY(dalloc(ctx, &ctx->d_ypro32, BN));
+    TRY(dalloc(ctx, &ctx->d_tmp32, BN));
+    TRY(dalloc(ctx, &ctx->d_d32, BN));
+    CK(cudaMemset(ctx->d_p64, 0, 2 * BN * sizeof(double)));
+    CK(cudaMemset(ctx->d_p32, 0, 2 * BN * sizeof(float)));
+    CK(cudaMemset(ctx->d_r64, 0, 2 * BN * sizeof(double)));
+    CK(cudaMemset(ctx->d_r32, 0, 2 * BN * sizeof(float)));
+    TRY(dalloc(ctx, &ctx->d_e64, (size_t)B * nbp));
+    TRY(dalloc(ctx, &ctx->d_e32, (size_t)B * ctx->nbp32));
+    CK(cudaMemset(ctx->d_e32, 0, (size_t)B * ctx->nbp32 * sizeof(float)));
+    TRY(dalloc(ctx, &ctx->d_L, (size_t)B * nbp * nbp));
+    TRY(dalloc(ctx, &ctx->d_mu, (size_t)B * ctx->n_mu));
+    TRY(dalloc(ctx, &ctx->d_st, B));
+    ctx->max_tiles = std::max(tiles_flat(N), tiles_box(g));
+    TRY(dalloc(ctx, &ctx->d_part, (size_t)B * ctx->max_tiles * 4));
+    ctx->nsplit = (int)std::max<long long>(1, std::min<long long>(64, N / 4096));
+    TRY(dalloc(ctx, &ctx->d_proj, (size_t)ctx->nsplit * B * nbp));
+    TRY(dalloc(ctx, &ctx->d_tick, B));
+    CK(cudaMemset(ctx->d_tick, 0, B * sizeof(unsigned)));
+    TRY(dalloc(ctx, &ctx->d_lcnt, N_LISTS));
+    TRY(dalloc(ctx, &ctx->d_lidx, (size_t)N_LISTS * B));
+    TRY(dalloc(ctx, &ctx->d_ndone, 1));
+    ctx->scratch_bytes = std::max<size_t>((size_t)128 * 128 * 128 * sizeof(double), 4096);
+    TRY(dalloc(ctx, &ctx->d_scratch, ctx->scratch_bytes / sizeof(double)));
+    TRY(tc_init(ctx->tc, ctx->geo, B, ctx->nbp32, ctx->num_sms, ctx->err));
+
+    if (cudaMallocHost((void**)&ctx->h_st, (size_t)B * sizeof(QState)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_ndone, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "pinned host allocation failed";
+        return RB_ENOMEM;
+    }
+    return RB_OK;
+}
+
+void ctx_destroy(rb_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    tc_free(ctx->tc);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    if (ctx->h_ndone) cudaFreeHost(ctx->h_ndone);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+__global__ void k_w_copies(long long N, int nb, int nbp, int nbp32, const double* W64c, float* W32c, float* W32r) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)nbp32 * N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / nbp32;
+        const int k = (int)(idx % nbp32);
+        const double w = k < nb ? W64c[(size_t)k * N + i] : 0.0;
+        W32r[idx] = (float)w;
+        if (k < nbp) W32c[(size_t)k * N + i] = (float)w;
+    }
+}
+
+// Upload the reduced data of the current n and refresh the FP32 copies of W.
+rb_status ctx_refresh_basis(rb_ctx* ctx) {
+    const int n = ctx->n;
+    if (n > 0) {
+        CK(cudaMemcpy(ctx->d_ANq, ctx->h_ANq.data(), ctx->h_ANq.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_fNr, ctx->h_fNr.data(), ctx->h_fNr.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    k_w_copies<<<4096, 256, 0, ctx->own_stream>>>(ctx->N, n, ctx->nbp, ctx->nbp32, ctx->d_W64c, ctx->d_W32c,
+                                                  ctx->d_W32r);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->own_stream));
+    return RB_OK;
+}
+
+// rows [r0, r0 + rows) of a row-major [N][n] basis into the column-major W64c
+__global__ void k_scatter_rowmajor(long long N, long long r0, long long rows, int n, const double* Wrow,
+                                   double* W64c) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * rows;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / n;
+        const int k = (int)(idx % n);
+        W64c[(size_t)k * N + r0 + i] = Wrow[idx];
+    }
+}
+
+rb_status upload_basis(rb_ctx* ctx, int n, const double* W, const double* ANq, const double* fNr) {
+    ctx->n = n;
+    const size_t Q = ctx->P, R = ctx->R;
+    ctx->h_ANq.assign(ANq ? ANq : nullptr, ANq ? ANq + Q * n * n : nullptr);
+    ctx->h_fNr.assign(fNr ? fNr : nullptr, fNr ? fNr + R * n : nullptr);
+    ctx->h_Rsnap.assign((size_t)n * n, 0.0);
+    ctx->selected.assign(n, -1);
+    if (n > 0) {
+        // stage the row-major host W through the device in slices
+        const long long N = ctx->N;
+        const long long rows_per = std::max<long long>(1, (long long)(ctx->scratch_bytes / sizeof(double)) / n);
+        for (long long r0 = 0; r0 < N; r0 += rows_per) {
+            const long long rows = std::min(rows_per, N - r0);
+            CK(cudaMemcpy(ctx->d_scratch, W + r0 * n, (size_t)rows * n * sizeof(double), cudaMemcpyHostToDevice));
+            k_scatter_rowmajor<<<1024, 256>>>(N, r0, rows, n, ctx->d_scratch, ctx->d_W64c);
+            CK(cudaGetLastError());
+            CK(cudaDeviceSynchronize());
+        }
+    }
+    return ctx_refresh_basis(ctx);
+}
+
+}  // namespace
+
+// ============================================================================
+// solve drivers
+
+namespace {
+
+struct Mode {
+    bool rbi;
+    bool mixed;
+};
+
+Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m) {
+    Params P{};
+    P.g = ctx->geo;
+    P.B = B;
+    P.Bmax = ctx->Bmax;
+    P.n_mu = ctx->n_mu;
+    P.mu = ctx->d_mu;
+    P.R = ctx->R;
+    P.fr = ctx->d_fr;
+    for (int r = 0; r < ctx->R; ++r) P.load_param[r] = ctx->load_param[r];
+    P.nb = ctx->n;
+    P.nbp = ctx->nbp;
+    P.W64c = ctx->d_W64c;
+    P.W32c = ctx->d_W32c;
+    P.L = ctx->d_L;
+    P.x64 = x64;
+    if (m.mixed) {
+        P.r = ctx->d_r32; P.p = ctx->d_p32; P.y = ctx->d_y32; P.ypro = ctx->d_ypro32;
+        P.tmp = ctx->d_tmp32; P.d = ctx->d_d32; P.e = ctx->d_e32;
+    } else {
+        P.r = ctx->d_r64; P.p = ctx->d_p64; P.y = ctx->d_y64; P.ypro = ctx->d_ypro64;
+        P.tmp = ctx->d_tmp64; P.d = x64; P.e = ctx->d_e64;
+    }
+    P.st = ctx->d_st;
+    P.part = ctx->d_part;
+    P.max_tiles = ctx->max_tiles;
+    P.proj = ctx->d_proj;
+    P.nsplit = ctx->nsplit;
+    P.tick = ctx->d_tick;
+    P.lcnt = ctx->d_lcnt;
+    P.lidx = ctx->d_lidx;
+    P.ndone = ctx->d_ndone;
+    P.tol = o.tol;
+    P.inner_tol = o.inner_tol;
+    P.max_iter = o.max_iter;
+    P.max_outer = o.max_outer;
+    P.beta_form = o.beta_form;
+    P.smoother = o.smoother;
+    P.omega = o.omega;
+    P.mixed = m.mixed ? 1 : 0;
+    return P;
+}
+
+enum KernelKind {
+    KK_OUTER_UPDATE, KK_OUTER_RES, KK_RBI_RES, KK_PROJECT, KK_RSOLVE, KK_PROLONG, KK_SMOOTH, KK_CG_A, KK_CG_B,
+    KK_TC_PROJECT, KK_TC_PROLONG, KK_COUNT
+};
+const char* const KK_NAMES[KK_COUNT] = {"outer_update", "outer_residual", "rbi_residual", "project",
+                                        "reduced_solve", "prolong", "smooth", "cg_a", "cg_b",
+                                        "tc_project", "tc_prolong"};
+
+cudaEvent_t next_event(rb_ctx* ctx) {
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_used++];
+}
+
+// Run f; while profiling, bracket it with events on the step's stream.
+template <typename F>
+void timed(rb_ctx* ctx, int kind, cudaStream_t s, F&& f) {
+    if (!ctx->profiling) { f(); return; }
+    const size_t first = ctx->ev_used;
+    cudaEventRecord(next_event(ctx), s);
+    f();
+    cudaEventRecord(next_event(ctx), s);
+    ctx->prof_pending.push_back({kind, first});
+}
+
+// Accumulate the recorded launches (the stream has been synchronised).
+void flush_profile(rb_ctx* ctx) {
+    for (auto& pr : ctx->prof_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[pr.second], ctx->ev_pool[pr.second + 1]) == cudaSuccess) {
+            ctx->prof_ms[pr.first] += ms;
+            ctx->prof_launches[pr.first] += 1;
+        }
+    }
+    cudaGetLastError();
+    ctx->prof_pending.clear();
+    ctx->ev_used = 0;
+}
+
+// One step of the per-query state machine for every active query.
+void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
+    cudaStream_t s = L.s;
+    const bool rm = use_rowmarch(ctx->geo) && !ctx->force_generic;
+    if (m.rbi) {
+        timed(ctx, KK_RBI_RES, s, [&] { launch_rbi_residual(P, L); });
+        cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
+        timed(ctx, KK_PROJECT, s, [&] { launch_project<double>(P, L); });
+        timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<double>(P, L); });
+        timed(ctx, KK_PROLONG, s, [&] { launch_prolong<double>(P, L, true); });
+        timed(ctx, KK_SMOOTH, s, [&] { launch_smoother<double>(P, L, o.nu, true); });
+        cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
+        return;
+    }
+    if (m.mixed) {
+        timed(ctx, KK_OUTER_UPDATE, s, [&] { launch_outer_update(P, L); });
+        timed(ctx, KK_OUTER_RES, s, [&] { launch_outer_residual<float>(P, L); });
+    } else {
+        timed(ctx, KK_OUTER_RES, s, [&] { launch_outer_residual<double>(P, L); });
+    }
+    cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
+    if (m.mixed) {
+        if (use_tc) {
+            timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
+            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
+            timed(ctx, KK_TC_PROLONG, s, [&] { tc_prolong(ctx->tc, P, L, ctx->d_W32r); });
+        } else {
+            timed(ctx, KK_PROJECT, s, [&] { launch_project<float>(P, L); });
+            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
+            timed(ctx, KK_PROLONG, s, [&] { launch_prolong<float>(P, L, false); });
+        }
+        timed(ctx, KK_SMOOTH, s, [&] {
+            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
+            else launch_smoother<float>(P, L, o.nu, false);
+        });
+    } else {
+        timed(ctx, KK_PROJECT, s, [&] { launch_project<double>(P, L); });
+        timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<double>(P, L); });
+        timed(ctx, KK_PROLONG, s, [&] { launch_prolong<double>(P, L, false); });
+        timed(ctx, KK_SMOOTH, s, [&] {
+            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
+            else launch_smoother<double>(P, L, o.nu, false);
+        });
+    }
+    cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
+    if (m.mixed) {
+        timed(ctx, KK_CG_A, s, [&] { if (rm) launch2d_cg_a<float>(P, L); else launch_cg_a<float>(P, L); });
+        timed(ctx, KK_CG_B, s, [&] { if (rm) launch2d_cg_b<float>(P, L); else launch_cg_b<float>(P, L); });
+    } else {
+        timed(ctx, KK_CG_A, s, [&] { if (rm) launch2d_cg_a<double>(P, L); else launch_cg_a<double>(P, L); });
+        timed(ctx, KK_CG_B, s, [&] { if (rm) launch2d_cg_b<double>(P, L); else launch_cg_b<double>(P, L); });
+    }
+    cudaMemsetAsync(ctx->d_lcnt + L_ITER, 0, sizeof(int), s);
+}
+
+rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
+    if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
+        (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
+        (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED)) {
+        ctx->err = "invalid options";
+        return RB_EINVAL;
+    }
+    return RB_OK;
+}
+
+// Solve one wave of B <= Bmax queries; x64 is a device array [B][N].
+rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool x_given, const rb_opts& o, Mode m,
+                   rb_stats* stats) {
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
+    const long long N = ctx->N;
+    for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i) {
+        if (!std::isfinite(mu_host[i])) {
+            ctx->err = "parameter vector holds a non-finite value";
+            return RB_EINVAL;
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->d_mu, mu_host, (size_t)B * ctx->n_mu * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int q = 0; q < B; ++q) {
+        QState& st = ctx->h_st[q];
+        std::memset(&st, 0, sizeof(QState));
+        st.phase = PH_OUTER;
+        st.start = 1;
+        st.xzero = x_given ? 0 : 1;
+    }
+    CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
+    std::vector<int> lc(N_LISTS, 0);
+    lc[L_OUT] = B;
+    std::vector<int> li(B);
+    for (int q = 0; q < B; ++q) li[q] = q;
+    CK(cudaMemcpyAsync(ctx->d_lcnt, lc.data(), N_LISTS * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lidx + L_OUT * ctx->Bmax, li.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_ndone, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(ctx->d_tick, 0, (size_t)B * sizeof(unsigned), s));
+    if (!x_given) CK(cudaMemsetAsync(x64, 0, (size_t)B * N * sizeof(double), s));
+    if (m.mixed) CK(cudaMemsetAsync(ctx->d_d32, 0, (size_t)B * N * sizeof(float), s));
+
+    Params P = make_params(ctx, B, x64, o, m);
+    Launch L{ctx->grid, s};
+    launch_cholesky(P, s, ctx->d_ANq, ctx->P);
+    CK(cudaGetLastError());
+
+    const bool use_tc = m.mixed && o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
+    const int check_every = 8;
+    cudaGraphExec_t exec = nullptr;
+    if (o.graph && s != nullptr && !ctx->profiling) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < check_every; ++k) enqueue_step(ctx, P, L, o, m, use_tc);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (ce != cudaSuccess) {
+            ctx->err = std::string("graph capture failed: ") + cudaGetErrorString(ce);
+            return RB_ECUDA;
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            ctx->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ce);
+            return RB_ECUDA;
+        }
+    }
+    const long long max_steps = (long long)o.max_iter + 2LL * o.max_outer + 64;
+    long long steps = 0;
+    rb_status rs = RB_OK;
+    for (;;) {
+        if (exec) {
+            cudaError_t e = cudaGraphLaunch(exec, s);
+            if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); rs = RB_ECUDA; break; }
+        } else {
+            for (int k = 0; k < check_every; ++k) enqueue_step(ctx, P, L, o, m, use_tc);
+        }
+        steps += check_every;
+        cudaMemcpyAsync(ctx->h_ndone, ctx->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { ctx->err = std::string("solve failed: ") + cudaGetErrorString(e); rs = RB_ECUDA; break; }
+        if (ctx->profiling) flush_profile(ctx);
+        if (*ctx->h_ndone >= B) break;
+        if (steps > max_steps) {
+            ctx->err = "solver state machine did not finish within its step budget";
+            rs = RB_ETIMEOUT;
+            break;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (rs != RB_OK) return rs;
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, (size_t)B * sizeof(QState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rb_status worst = RB_OK;
+    for (int q = 0; q < B; ++q) {
+        const QState& st = ctx->h_st[q];
+        if (stats) {
+            stats[q].iters = st.iters;
+            stats[q].outer = st.outer;
+            stats[q].restarts = st.restarts;
+            stats[q].status = st.status;
+            stats[q].rel_res = st.rel_res;
+        }
+        if (st.status > (int)worst) worst = (rb_status)st.status;
+    }
+    return worst;
+}
+
+rb_status run_batch(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts* opts, rb_stats* stats, Mode m) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!mu || !x))) { ctx->err = "B < 0 or NULL mu / x"; return RB_EINVAL; }
+    rb_opts o;
+    rb_default_opts(&o);
+    if (opts) o = *opts;
+    TRY(validate_opts(ctx, o));
+    if (m.rbi) m.mixed = false;
+    else m.mixed = o.precision == RB_PREC_MIXED;
+    const bool dev_x = is_device_ptr(x);
+    const bool x_given = o.x0_mode == RB_X0_GIVEN;
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
+    const long long N = ctx->N;
+    rb_status worst = RB_OK;
+    for (int b0 = 0; b0 < B; b0 += ctx->Bmax) {
+        const int nbw = std::min(ctx->Bmax, B - b0);
+        double* x64 = dev_x ? x + (size_t)b0 * N : ctx->d_x64;
+        if (!dev_x && x_given)
+            CK(cudaMemcpyAsync(x64, x + (size_t)b0 * N, (size_t)nbw * N * sizeof(double), cudaMemcpyHostToDevice, s));
+        rb_status w = run_wave(ctx, nbw, mu + (size_t)b0 * ctx->n_mu, x64, x_given, o, m, stats ? stats + b0 : nullptr);
+        if (w == RB_EINVAL || w == RB_ECUDA || w == RB_ETIMEOUT) return w;
+        if (w > worst) worst = w;
+        if (!dev_x) {
+            CK(cudaMemcpyAsync(x + (size_t)b0 * N, x64, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+    return worst;
+}
+
+}  // namespace
+
+// ============================================================================
+// public API
+
+extern "C" {
+
+void rb_default_opts(rb_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 20000;
+    o->smoother = RB_SMOOTH_RBGS;
+    o->nu = 1;
+    o->omega = 2.0 / 3.0;
+    o->precision = RB_PREC_FP64;
+    o->beta_form = RB_BETA_PR;
+    o->x0_mode = RB_X0_ZERO;
+    o->inner_tol = 1e-5;
+    o->max_outer = 12;
+    o->gemm = RB_GEMM_AUTO;
+    o->graph = 1;
+    o->stream = nullptr;
+}
+
+void rb_default_build_opts(rb_build_opts* o) {
+    if (!o) return;
+    o->truth_tol = 1e-11;
+    o->truth_max_iter = 200000;
+    o->score = 0;
+    o->drop_tol = 1e-10;
+}
+
+const char* rb_status_string(rb_status s) {
+    switch (s) {
+        case RB_OK: return "ok";
+        case RB_EINVAL: return "invalid argument";
+        case RB_ENOMEM: return "out of memory";
+        case RB_EFORMAT: return "malformed basis file";
+        case RB_ECUDA: return "CUDA error";
+        case RB_EBREAKDOWN: return "numerical breakdown";
+        case RB_ENOCONV: return "not converged";
+        case RB_ETIMEOUT: return "timeout";
+        case RB_EIO: return "I/O error";
+    }
+    return "unknown status";
+}
+
+const char* rb_last_error(const rb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void rb_free(rb_ctx* ctx) { ctx_destroy(ctx); }
+
+rb_status rb_offline_load_arrays(rb_ctx** out, const rb_problem* prob, int n, const double* W, const double* ANq,
+                                 const double* fNr, int max_batch) {
+    if (!out) { g_create_error = "out is NULL"; return RB_EINVAL; }
+    *out = nullptr;
+    std::string why;
+    rb_status v = validate_problem(prob, why);
+    if (v != RB_OK) { g_create_error = why; return v; }
+    if (n < 0 || n > MAX_N || max_batch < 1 || (n > 0 && (!W || !ANq || !fNr))) {
+        g_create_error = "need 0 <= n <= 128, max_batch >= 1 and non-NULL W, ANq, fNr";
+        return RB_EINVAL;
+    }
+    rb_ctx* ctx = new rb_ctx();
+    rb_status s = ctx_init(ctx, prob, n, max_batch);
+    if (s == RB_OK) s = upload_basis(ctx, n, W, ANq, fNr);
+    if (s != RB_OK) {
+        g_create_error = ctx->err;
+        ctx_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return RB_OK;
+}
+
+rb_status rb_info(const rb_ctx* ctx, long long* n_dof, int* n, int* Q, int* R, int* n_mu) {
+    if (!ctx) return RB_EINVAL;
+    if (n_dof) *n_dof = ctx->N;
+    if (n) *n = ctx->n;
+    if (Q) *Q = ctx->P;
+    if (R) *R = ctx->R;
+    if (n_mu) *n_mu = ctx->n_mu;
+    return RB_OK;
+}
+
+rb_status rb_profile(rb_ctx* ctx, int enable) {
+    if (!ctx) return RB_EINVAL;
+    ctx->profiling = enable != 0;
+    if (enable) {
+        for (int k = 0; k < 32; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_launches[k] = 0; }
+        ctx->prof_pending.clear();
+        ctx->ev_used = 0;
+    }
+    return RB_OK;
+}
+
+rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* count) {
+    if (!ctx || (cap > 0 && !out)) return RB_EINVAL;
+    int c = 0;
+    for (int k = 0; k < KK_COUNT; ++k) {
+        if (ctx->prof_launches[k] == 0) continue;
+        if (c < cap) {
+            std::memset(out[c].name, 0, sizeof(out[c].name));
+            std::strncpy(out[c].name, KK_NAMES[k], sizeof(out[c].name) - 1);
+            out[c].launches = ctx->prof_launches[k];
+            out[c].ms = ctx->prof_ms[k];
+        }
+        ++c;
+    }
+    if (count) *count = c;
+    return RB_OK;
+}
+
+rb_status rb_solve(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts* opts, rb_stats* stats) {
+    return run_batch(ctx, B, mu, x, opts, stats, Mode{true, false});
+}
+
+rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts* opts, rb_stats* stats) {
+    return run_batch(ctx, B, mu, x, opts, stats, Mode{false, false});
+}
+
+rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y, void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!mu || !x || !y))) { ctx->err = "B < 0 or NULL argument"; return RB_EINVAL; }
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+    for (int b0 = 0; b0 < B; b0 += ctx->Bmax) {
+        const int nbw = std::min(ctx->Bmax, B - b0);
+        for (size_t i = 0; i < (size_t)nbw * ctx->n_mu; ++i)
+            if (!std::isfinite(mu[(size_t)b0 * ctx->n_mu + i])) { ctx->err = "non-finite parameter"; return RB_EINVAL; }
+        CK(cudaMemcpyAsync(ctx->d_mu, mu + (size_t)b0 * ctx->n_mu, (size_t)nbw * ctx->n_mu * sizeof(double),
+                           cudaMemcpyHostToDevice, s));
+        const double* xs = dx ? x + (size_t)b0 * N : ctx->d_x64;
+        double* ys = dy ? y + (size_t)b0 * N : ctx->d_y64;
+        if (!dx) CK(cudaMemcpyAsync(ctx->d_x64, x + (size_t)b0 * N, (size_t)nbw * N * sizeof(double),
+                                    cudaMemcpyHostToDevice, s));
+        launch_apply(ctx->geo, nbw, ctx->n_mu, ctx->d_mu, xs, ys, s);
+        CK(cudaGetLastError());
+        if (!dy) CK(cudaMemcpyAsync(y + (size_t)b0 * N, ys, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RB_OK;
+}
+
+}  // extern "C"
+
+#include "rb_offline.inl"

@@ -1,0 +1,263 @@
+// Internal declarations shared by the librb translation units.
+//
+// Data layout in HBM (per context):
+//   W64c  [nbp][N]   FP64 basis, column-major (basis vector k contiguous)
+//   W32c  [nbp][N]   FP32 copy (K-major operand of the batched projection)
+//   W32r  [N][nbp32] FP32 copy, row-major (K-major operand of the prolongation)
+//   fr    [R][N]     FP64 load terms f_r (eq. 12)
+//   batch vectors [B][N] per buffer, query-major, x fastest; residual and
+//   search direction are ping-ponged ([2][B][N]) so that a stencil kernel never
+//   reads a neighbour that another CTA of the same launch has already rewritten.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rb.h"
+
+namespace rbk {
+
+constexpr int MAX_P = 64;        // blocks (affine terms)
+constexpr int MAX_MU = 128;      // entries of one parameter vector
+constexpr int MAX_LOADS = 8;
+constexpr int MAX_N = 128;       // basis size
+constexpr int THREADS = 256;     // CTA size of the streaming kernels
+constexpr int TILE = 1024;       // points per flat tile (4 per thread)
+
+// Geometry of the grid and of the block partition.
+struct Geo {
+    int dim, mx, my, mz;
+    int nbx, nby, nbz, P;
+    long long n;                 // N_dof
+    double ihx2, ihy2, ihz2;     // 1/h_d^2
+    const int* bx;               // block index along x of every node column, [mx]
+    const int* by;               // [my]
+    const int* bz;               // [mz]
+};
+
+// Per-query phase of the solver state machine.
+enum Phase : int {
+    PH_OUTER = 0,    // needs an FP64 residual f - A x (start, refinement step, final check)
+    PH_PREC = 1,     // needs the RBI preconditioner y = RBI(A, r, W, 1)
+    PH_ITER = 2,     // in the CG body (q = A p, alpha, updates)
+    PH_DONE = 3
+};
+
+// Work lists (one per phase that a kernel consumes).
+enum ListId : int { L_OUT = 0, L_PREC = 1, L_ITER = 2, N_LISTS = 3 };
+
+struct QState {
+    double fnorm;        // ||f(mu)||
+    double target;       // absolute residual target of the current CG cycle
+    double rho;          // r^T y of the current cycle
+    double alpha, beta;
+    double rnorm;        // last recurrence residual norm
+    double rel_res;      // last true relative residual (FP64)
+    int iters, outer, restarts, status;
+    int phase;
+    int start;           // 1: the next preconditioner output starts a CG cycle (beta = 0)
+    int rpar, ppar;      // current halves of the r and p ping-pong buffers
+    int xzero;           // x is exactly zero (skip A x in the residual)
+    int pad_;
+};
+
+// Everything a solver kernel needs; passed by value.
+struct Params {
+    Geo g;
+    int B;                       // slots in this wave
+    int Bmax;
+    int n_mu;
+    const double* mu;            // [B][n_mu]
+    int R;
+    const double* fr;            // [R][N]
+    int load_param[MAX_LOADS];
+    // basis
+    int nb, nbp;                 // basis size and padded stride
+    const double* W64c;
+    const float* W32c;
+    const double* L;             // [Bmax][nbp][nbp] Cholesky factors (lower, row-major)
+    // vectors
+    double* x64;                 // [B][N] FP64 iterate / solution
+    void* r;                     // [2][B][N] of T
+    void* p;                     // [2][B][N] of T
+    void* y;                     // [B][N] of T
+    void* ypro;                  // [B][N] of T
+    void* tmp;                   // [B][N] of T (smoother ping-pong for nu >= 2)
+    void* d;                     // [B][N] of T: inner iterate (aliases x64 in FP64 mode)
+    void* e;                     // [B][nbp] of T: reduced correction e_N
+    // reductions and lists
+    QState* st;
+    double* part;                // [B][max_tiles][4]
+    int max_tiles;
+    double* proj;                // [nsplit][B][nbp] partial W^T r
+    int nsplit;
+    unsigned* tick;              // [B] arrival counters
+    int* lcnt;                   // [N_LISTS]
+    int* lidx;                   // [N_LISTS][Bmax]
+    int* ndone;                  // queries that reached PH_DONE
+    // options
+    double tol, inner_tol;
+    int max_iter, max_outer;
+    int beta_form, smoother;
+    double omega;
+    int mixed;                   // 1: T = float inner with FP64 refinement
+};
+
+// ----------------------------------------------------------------------------
+// small device helpers
+
+// (ix, iy, iz) of flat index i; N_dof < 2^31 is enforced at context creation
+__device__ __forceinline__ void node_xyz(const Geo& g, long long i, int& ix, int& iy, int& iz) {
+    const unsigned ii = (unsigned)i;
+    const unsigned t = ii / (unsigned)g.mx;
+    ix = (int)(ii - t * (unsigned)g.mx);
+    iz = (int)(t / (unsigned)g.my);
+    iy = (int)(t - (unsigned)iz * (unsigned)g.my);
+}
+
+// Face coefficients kappa_f / h^2 of one node (zero where the face is missing
+// is NOT used: a missing neighbour has value 0, the face still counts in the
+// diagonal with kappa = mu_p(i)).
+template <typename T>
+struct Coef {
+    T kxm, kxp, kym, kyp, kzm, kzp, diag;
+};
+
+template <typename T>
+__device__ __forceinline__ void node_coef(const Geo& g, const T* __restrict__ mus, int ix, int iy, int iz,
+                                          Coef<T>& c) {
+    const int bxc = __ldg(g.bx + ix), byc = __ldg(g.by + iy), bzc = __ldg(g.bz + iz);
+    const int pyz = g.nbx * (byc + g.nby * bzc);
+    const T m = mus[bxc + pyz];
+    const T half = T(0.5);
+    const T hx = (T)g.ihx2, hy = (T)g.ihy2, hz = (T)g.ihz2;
+    c.kxm = hx * (ix > 0 ? half * (m + mus[__ldg(g.bx + ix - 1) + pyz]) : m);
+    c.kxp = hx * (ix < g.mx - 1 ? half * (m + mus[__ldg(g.bx + ix + 1) + pyz]) : m);
+    const int pxz = bxc + g.nbx * g.nby * bzc;
+    c.kym = hy * (iy > 0 ? half * (m + mus[pxz + g.nbx * __ldg(g.by + iy - 1)]) : m);
+    c.kyp = hy * (iy < g.my - 1 ? half * (m + mus[pxz + g.nbx * __ldg(g.by + iy + 1)]) : m);
+    T dg = c.kxm + c.kxp + c.kym + c.kyp;
+    if (g.dim == 3) {
+        const int pxy = bxc + g.nbx * byc;
+        c.kzm = hz * (iz > 0 ? half * (m + mus[pxy + g.nbx * g.nby * __ldg(g.bz + iz - 1)]) : m);
+        c.kzp = hz * (iz < g.mz - 1 ? half * (m + mus[pxy + g.nbx * g.nby * __ldg(g.bz + iz + 1)]) : m);
+        dg += c.kzm + c.kzp;
+    } else {
+        c.kzm = c.kzp = T(0);
+    }
+    c.diag = dg;
+}
+
+// sum over the faces of node i of kappa_f/h^2 * v_j (v_j = 0 outside the grid)
+template <typename T, typename Get>
+__device__ __forceinline__ T offdiag_sum(const Geo& g, const Coef<T>& c, long long i, int ix, int iy, int iz,
+                                         Get get) {
+    T s = T(0);
+    if (ix > 0) s += c.kxm * get(i - 1);
+    if (ix < g.mx - 1) s += c.kxp * get(i + 1);
+    if (iy > 0) s += c.kym * get(i - g.mx);
+    if (iy < g.my - 1) s += c.kyp * get(i + g.mx);
+    if (g.dim == 3) {
+        const long long pl = (long long)g.mx * g.my;
+        if (iz > 0) s += c.kzm * get(i - pl);
+        if (iz < g.mz - 1) s += c.kzp * get(i + pl);
+    }
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red /* >= 32 entries */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void list_push(const Params& P, int list, int q) {
+    const int pos = atomicAdd(P.lcnt + list, 1);
+    P.lidx[list * P.Bmax + pos] = q;
+}
+
+__device__ __forceinline__ void mark_done(const Params& P, QState& s, int status) {
+    s.phase = PH_DONE;
+    s.status = status;
+    atomicAdd(P.ndone, 1);
+}
+
+// Thread 0 publishes a CTA's partial sums for (q, tile); returns true in every
+// thread of the CTA that is the last to do so for q.  The caller then reduces
+// the partials in a fixed order (deterministic) and resets tick[q].
+__device__ __forceinline__ bool arrive(const Params& P, int q, int tile, int ntiles, const double* vals, int nv) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        double* dst = P.part + ((size_t)q * P.max_tiles + tile) * 4;
+        for (int j = 0; j < nv; ++j) dst[j] = vals[j];
+        __threadfence();
+        const unsigned prev = atomicAdd(P.tick + q, 1u);
+        s_last = (prev == (unsigned)ntiles - 1u);
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// Fixed-order sum of the partials of q; result in out[0..nv) of thread 0.
+__device__ __forceinline__ void gather_partials(const Params& P, int q, int ntiles, int nv, double* out,
+                                                double* red) {
+    for (int j = 0; j < nv; ++j) {
+        double s = 0.0;
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+            s += __ldcg(P.part + ((size_t)q * P.max_tiles + t) * 4 + j);
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) out[j] = s;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launch wrappers (defined in the .cu files)
+
+struct Launch {
+    int grid;          // persistent grid size of the streaming kernels
+    cudaStream_t s;
+};
+
+template <typename T> void launch_outer_residual(const Params& P, const Launch& L);
+void launch_outer_update(const Params& P, const Launch& L);
+template <typename T> void launch_project(const Params& P, const Launch& L);
+template <typename T> void launch_reduced_solve(const Params& P, const Launch& L);
+template <typename T> void launch_prolong(const Params& P, const Launch& L, bool rbi_mode);
+template <typename T> void launch_smoother(const Params& P, const Launch& L, int nu, bool rbi_mode);
+// row-marching 2D variants (dim 2, mx a multiple of 128, mx <= 1024)
+bool use_rowmarch(const Geo& g);
+template <typename T> void launch2d_cg_a(const Params& P, const Launch& L);
+template <typename T> void launch2d_cg_b(const Params& P, const Launch& L);
+template <typename T> void launch2d_smooth(const Params& P, const Launch& L, int nu);
+template <typename T> void launch_cg_a(const Params& P, const Launch& L);
+template <typename T> void launch_cg_b(const Params& P, const Launch& L);
+void launch_rbi_residual(const Params& P, const Launch& L);
+void launch_cholesky(const Params& P, cudaStream_t s, const double* ANq, int Q);
+void launch_apply(const Geo& g, int B, int n_mu, const double* mu, const double* x, double* y, cudaStream_t s);
+void launch_fill_loads(const Geo& g, int R, const int* kind, const double* center, const double* sigma,
+                       double* fr, cudaStream_t s);
+
+// offline-build helpers
+void launch_project_cols(const Geo& g, int nb, const double* W64c, int nv, const double* V, double* out,
+                         double* scratch, cudaStream_t s);                 // out[v][k] = W[:,k]^T V[v]
+void launch_sub_cols(const Geo& g, int nb, const double* W64c, const double* c, double* v, cudaStream_t s);
+void launch_scores(const Geo& g, int P, int R, const int* load_param, int n_mu, int nb, int nbp,
+                   const double* ANq, const double* fNr, const double* Rsnap, int ntrain, const double* mu,
+                   int literal, double* score, int* bad, cudaStream_t s);
+double launch_norm(const Geo& g, const double* v, double* scratch, cudaStream_t s);
+
+int tiles_flat(long long n);
+int tiles_box(const Geo& g);
+
+}  // namespace rbk

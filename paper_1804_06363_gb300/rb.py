@@ -1,0 +1,296 @@
+"""ctypes binding of librb (include/rb.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Arrays may be numpy arrays (host
+memory) or any object exposing ``__cuda_array_interface__`` (device memory,
+e.g. a CUDA tensor); plain integers are taken as raw device pointers.  If the
+library is missing this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librb.so")
+
+RB_OK, RB_EINVAL, RB_ENOMEM, RB_EFORMAT, RB_ECUDA, RB_EBREAKDOWN, RB_ENOCONV, RB_ETIMEOUT, RB_EIO = range(9)
+STATUS_NAMES = ["ok", "einval", "enomem", "eformat", "ecuda", "ebreakdown", "enoconv", "etimeout", "eio"]
+SMOOTHERS = {"none": 0, "rbgs": 1, "jacobi": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+BETAS = {"fr": 0, "pr": 1}
+GEMMS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
+
+
+class RbLoad(C.Structure):
+    _fields_ = [("kind", C.c_int), ("param", C.c_int), ("center", C.c_double * 3), ("sigma", C.c_double)]
+
+
+class RbProblem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("m", C.c_int * 3), ("nb", C.c_int * 3), ("n_loads", C.c_int),
+                ("loads", C.POINTER(RbLoad)), ("n_mu", C.c_int)]
+
+
+class RbOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("smoother", C.c_int), ("nu", C.c_int),
+                ("omega", C.c_double), ("precision", C.c_int), ("beta_form", C.c_int), ("x0_mode", C.c_int),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("gemm", C.c_int), ("graph", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class RbStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("rel_res", C.c_double)]
+
+
+class RbBuildOpts(C.Structure):
+    _fields_ = [("truth_tol", C.c_double), ("truth_max_iter", C.c_int), ("score", C.c_int),
+                ("drop_tol", C.c_double)]
+
+
+class RbKernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_longlong), ("ms", C.c_double)]
+
+
+_lib = None
+
+# every function declared in include/rb.h, with its ctypes signature
+SIGNATURES = {
+    "rb_default_opts": (None, [C.POINTER(RbOpts)]),
+    "rb_default_build_opts": (None, [C.POINTER(RbBuildOpts)]),
+    "rb_offline_load_arrays": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(RbProblem), C.c_int, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_int]),
+    "rb_offline_build": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(RbProblem), C.c_int, C.c_int, C.c_void_p,
+                                   C.POINTER(RbBuildOpts), C.POINTER(RbOpts), C.c_int]),
+    "rb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "rb_offline_load": (C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_int]),
+    "rb_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                          C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "rb_get_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
+    "rb_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
+    "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
+    "rb_last_error": (C.c_char_p, [C.c_void_p]),
+    "rb_status_string": (C.c_char_p, [C.c_int]),
+    "rb_free": (None, [C.c_void_p]),
+}
+
+
+def lib() -> C.CDLL:
+    """Load librb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1804_06363_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _ptr(a) -> int:
+    """Raw address of a host (numpy) or device (__cuda_array_interface__) array, or an int."""
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    cai = getattr(a, "__cuda_array_interface__", None)
+    if cai is not None:
+        if cai.get("strides") is not None:
+            raise ValueError("device arrays must be contiguous")
+        return int(cai["data"][0])
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_problem(prob):
+    """rb_problem from a problem description with dims, blocks, loads and n_mu."""
+    dims = list(prob.dims) + [1] * (3 - len(prob.dims))
+    blocks = list(prob.blocks) + [1] * (3 - len(prob.blocks))
+    loads = (RbLoad * len(prob.loads))()
+    for i, ld in enumerate(prob.loads):
+        loads[i].kind = 0 if ld.kind == "const" else 1
+        loads[i].param = ld.param
+        for j in range(3):
+            loads[i].center[j] = ld.center[j]
+        loads[i].sigma = ld.sigma
+    p = RbProblem()
+    p.dim = len(prob.dims)
+    for j in range(3):
+        p.m[j] = dims[j]
+        p.nb[j] = blocks[j]
+    p.n_loads = len(prob.loads)
+    p.loads = C.cast(loads, C.POINTER(RbLoad))
+    p.n_mu = prob.n_mu
+    return p, loads
+
+
+def make_opts(**kw) -> RbOpts:
+    o = RbOpts()
+    lib().rb_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "smoother":
+            v = SMOOTHERS[v] if isinstance(v, str) else v
+        elif k == "precision":
+            v = PRECISIONS[v] if isinstance(v, str) else v
+        elif k == "beta":
+            k, v = "beta_form", BETAS[v] if isinstance(v, str) else v
+        elif k == "gemm":
+            v = GEMMS[v] if isinstance(v, str) else v
+        elif k == "x0":
+            k, v = "x0_mode", 1 if v else 0
+        elif k == "stream":
+            v = C.c_void_p(int(v) if v else 0)
+        elif k == "graph":
+            v = int(bool(v))
+        setattr(o, k, v)
+    return o
+
+
+def stats_array(st) -> np.ndarray:
+    n = len(st)
+    out = np.zeros(n, dtype=[("iters", "i4"), ("outer", "i4"), ("restarts", "i4"), ("status", "i4"),
+                             ("rel_res", "f8")])
+    for i in range(n):
+        out[i] = (st[i].iters, st[i].outer, st[i].restarts, st[i].status, st[i].rel_res)
+    return out
+
+
+class Context:
+    """An online RB context (rb_ctx*)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+        n_dof, n, Q, R, n_mu = C.c_longlong(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib().rb_info(self._h, C.byref(n_dof), C.byref(n), C.byref(Q), C.byref(R), C.byref(n_mu))
+        self.n_dof, self.n, self.Q, self.R, self.n_mu = n_dof.value, n.value, Q.value, R.value, n_mu.value
+
+    # -- creation
+    @classmethod
+    def _check_create(cls, st, h):
+        if st != RB_OK:
+            raise RbError(st, lib().rb_last_error(None).decode())
+        return cls(h)
+
+    @classmethod
+    def from_arrays(cls, prob, W, ANq, fNr, max_batch: int = 1) -> "Context":
+        """rb_offline_load_arrays: W [N_dof][n], ANq [Q][n][n], fNr [R][n] (host)."""
+        p, keep = make_problem(prob)
+        W, ANq, fNr = _f64(W), _f64(ANq), _f64(fNr)
+        n = W.shape[1] if W.ndim == 2 else 0
+        h = C.c_void_p()
+        st = lib().rb_offline_load_arrays(C.byref(h), C.byref(p), n, _ptr(W), _ptr(ANq), _ptr(fNr), max_batch)
+        return cls._check_create(st, h)
+
+    @classmethod
+    def build(cls, prob, n_max: int, train_mu, max_batch: int = 1, truth_tol: float = 1e-11,
+              literal_score: bool = False, **solve_kw) -> "Context":
+        """rb_offline_build: greedy basis of size n_max from the training parameters (host)."""
+        p, keep = make_problem(prob)
+        mu = _f64(train_mu)
+        b = RbBuildOpts()
+        lib().rb_default_build_opts(C.byref(b))
+        b.truth_tol = truth_tol
+        b.score = 1 if literal_score else 0
+        o = make_opts(**solve_kw)
+        h = C.c_void_p()
+        st = lib().rb_offline_build(C.byref(h), C.byref(p), n_max, mu.shape[0], _ptr(mu), C.byref(b), C.byref(o),
+                                    max_batch)
+        return cls._check_create(st, h)
+
+    @classmethod
+    def load(cls, path: str, max_batch: int = 1) -> "Context":
+        h = C.c_void_p()
+        st = lib().rb_offline_load(C.byref(h), path.encode(), max_batch)
+        return cls._check_create(st, h)
+
+    # -- use
+    def _check(self, st):
+        if st not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN):
+            raise RbError(st, lib().rb_last_error(self._h).decode())
+        return st
+
+    def save(self, path: str) -> None:
+        self._check(lib().rb_save(self._h, path.encode()))
+
+    def basis(self):
+        n, N = self.n, self.n_dof
+        W = np.zeros((N, n))
+        ANq = np.zeros((self.Q, n, n))
+        fNr = np.zeros((self.R, n))
+        Rs = np.zeros((n, n))
+        sel = np.zeros(n, dtype=np.int32)
+        self._check(lib().rb_get_basis(self._h, _ptr(W), _ptr(ANq), _ptr(fNr), _ptr(Rs), _ptr(sel)))
+        return W, ANq, fNr, Rs, sel
+
+    def _run(self, fn, mu, x, kw):
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        B = mu.shape[0]
+        st = (RbStats * max(B, 1))()
+        o = make_opts(**kw)
+        status = fn(self._h, B, _ptr(mu), _ptr(x), C.byref(o), C.cast(st, C.c_void_p))
+        self._check(status)
+        return status, stats_array(st)[:B]
+
+    def solve(self, mu, x, **kw):
+        """rb_solve (RBI, Alg. 2).  x: [B][N_dof] host or device; returns (status, stats)."""
+        return self._run(lib().rb_solve, mu, x, kw)
+
+    def pcg(self, mu, x, **kw):
+        """rb_pcg (RBCG, Alg. 3).  x: [B][N_dof] host or device; returns (status, stats)."""
+        return self._run(lib().rb_pcg, mu, x, kw)
+
+    def apply(self, mu, x, y, stream: Optional[int] = None) -> None:
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        self._check(lib().rb_apply(self._h, mu.shape[0], _ptr(mu), _ptr(x), _ptr(y),
+                                   C.c_void_p(int(stream) if stream else 0)))
+
+    def profile(self, enable: bool) -> None:
+        """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""
+        self._check(lib().rb_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """rb_profile_read: {kernel name: (launches, device ms)}."""
+        buf = (RbKernelTime * 32)()
+        cnt = C.c_int()
+        self._check(lib().rb_profile_read(self._h, buf, 32, C.byref(cnt)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(min(cnt.value, 32))}
+
+    def close(self) -> None:
+        if self._h:
+            lib().rb_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

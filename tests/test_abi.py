@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/rb.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rb.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(rb_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1804_06363_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("rb_offline_load", "rb_offline_load_arrays", "rb_solve", "rb_pcg", "rb_apply",
+                     "rb_last_error", "rb_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in _declared_functions():
+        assert name in exported, name
+
+
+def test_binding_covers_the_header(libpath):
+    from paper_1804_06363_gb300 import rb
+    assert set(rb.SIGNATURES) == set(_declared_functions())
+    lib = rb.lib()
+    o = rb.make_opts()
+    assert o.tol == 1e-10 and o.nu == 1 and o.beta_form == rb.BETAS["pr"]
+    assert lib.rb_status_string(rb.RB_ENOCONV) == b"not converged"
+
+
+def test_struct_layouts_match_header(libpath):
+    """Field order / sizes of the ctypes mirrors agree with the C structs."""
+    from paper_1804_06363_gb300 import rb
+    assert ctypes.sizeof(rb.RbLoad) == 4 + 4 + 24 + 8
+    assert ctypes.sizeof(rb.RbStats) == 4 * 4 + 8
+    assert rb.RbOpts.stream.offset == ctypes.sizeof(rb.RbOpts) - 8
+
+
+def test_invalid_problem_is_rejected_without_gpu(libpath):
+    """Argument validation runs before any CUDA call."""
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+    prob = wl.small((8, 8), (2, 2), n_basis=1).problem
+    p, keep = rb.make_problem(prob)
+    p.dim = 4
+    h = ctypes.c_void_p()
+    st = rb.lib().rb_offline_load_arrays(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, 1)
+    assert st == rb.RB_EINVAL and not h.value
+    assert b"dim" in rb.lib().rb_last_error(None)

@@ -1,0 +1,276 @@
+"""GPU parity: librb (through the C interface) against the FP64 oracle.
+
+Bars: solutions within relative L2 1e-9 of the oracle's truth x(mu) at true
+relative residual 1e-10; FP64 iteration counts equal to the oracle's Alg. 2 /
+Alg. 3 replica up to reduction-order round-off (+-2 iterations).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import direct, greedy, rb as orb
+from oracle import problem as pb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1804_06363_gb300 import rb  # noqa: E402
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def case2d():
+    w = wl.small((40, 36), (3, 3), n_basis=8, n_train=40, bumps=True)
+    basis = greedy.greedy(w.problem, w.train_mu(), w.n_basis)
+    mu = w.test_mu(6)
+    truth = np.stack([direct.sparse_direct(w.problem, m) for m in mu])
+    ctx = rb.Context.from_arrays(w.problem, basis.W, basis.ANq, basis.fNr, max_batch=6)
+    yield w, basis, mu, truth, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,blocks,bumps", [((37, 29), (3, 2), True), ((13, 11, 9), (2, 2, 2), True),
+                                               ((64, 64), (2, 2), False), ((5, 1), (1, 1), False)])
+def test_apply_matches_oracle(dims, blocks, bumps):
+    w = wl.small(dims, blocks, n_basis=1, bumps=bumps)
+    prob = w.problem
+    ctx = rb.Context.from_arrays(prob, np.zeros((prob.n_dof, 0)), np.zeros((prob.P, 0, 0)),
+                                 np.zeros((len(prob.loads), 0)), max_batch=2)
+    rng = np.random.default_rng(0)
+    mu = w.test_mu(3)
+    x = rng.standard_normal((3, prob.n_dof))
+    ref = np.stack([pb.apply(prob, mu[b], x[b]) for b in range(3)])
+    yd = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+    ctx.apply(mu, _dev(x), yd)                       # device buffers, two waves (max_batch 2)
+    yh = np.zeros((3, prob.n_dof))
+    ctx.apply(mu, x, yh)                             # host buffers
+    for b in range(3):
+        assert _rel(yd[b].cpu().numpy(), ref[b]) < 1e-14
+        assert _rel(yh[b], ref[b]) < 1e-14
+    ctx.close()
+
+
+def test_rbi_matches_oracle(case2d):
+    w, basis, mu, truth, ctx = case2d
+    x = torch.zeros((len(mu), w.problem.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.solve(mu, x)
+    assert status == rb.RB_OK
+    xs = x.cpu().numpy()
+    for b in range(len(mu)):
+        ref = orb.rbi(basis, mu[b], tol=1e-10)
+        assert st["status"][b] == rb.RB_OK and st["rel_res"][b] < 1e-10
+        assert _rel(xs[b], truth[b]) < 1e-9
+        assert abs(int(st["iters"][b]) - ref.iters) <= 2, (st[b], ref.iters)
+
+
+@pytest.mark.parametrize("beta", ["fr", "pr"])
+def test_rbcg_fp64_matches_oracle_replica(case2d, beta):
+    """Same iterations and outcome as the oracle's Alg. 3, including the Fletcher-Reeves
+    stalls the non-symmetric RBI preconditioner causes for some parameters."""
+    w, basis, mu, truth, ctx = case2d
+    budget = 1500
+    x = torch.zeros((len(mu), w.problem.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu, x, beta=beta, precision="fp64", max_iter=budget)
+    xs = x.cpu().numpy()
+    for b in range(len(mu)):
+        ref = orb.rbcg(basis, mu[b], tol=1e-10, beta=beta, max_iter=budget)
+        if ref.converged:
+            assert st["status"][b] == rb.RB_OK and st["rel_res"][b] < 1e-10
+            assert _rel(xs[b], truth[b]) < 1e-9
+            assert abs(int(st["iters"][b]) - ref.iters) <= 2, (st[b], ref.iters)
+            assert int(st["restarts"][b]) == ref.restarts
+        else:
+            assert st["status"][b] == rb.RB_ENOCONV and int(st["iters"][b]) == budget
+    if beta == "pr":
+        assert status == rb.RB_OK
+
+
+@pytest.mark.parametrize("gemm", ["cuda_cores", "auto"])
+def test_rbcg_mixed_reaches_truth(case2d, gemm):
+    w, basis, mu, truth, ctx = case2d
+    x = torch.zeros((len(mu), w.problem.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu, x, precision="mixed", gemm=gemm)
+    assert status == rb.RB_OK, st
+    xs = x.cpu().numpy()
+    for b in range(len(mu)):
+        assert st["rel_res"][b] < 1e-10
+        assert _rel(xs[b], truth[b]) < 1e-9
+        r = pb.load(w.problem, mu[b]) - pb.apply(w.problem, mu[b], xs[b])
+        assert np.linalg.norm(r) / np.linalg.norm(pb.load(w.problem, mu[b])) < 1e-10
+
+
+def test_waves_host_buffers_and_determinism(case2d):
+    w, basis, mu, truth, _ = case2d
+    prob = w.problem
+    mu9 = w.test_mu(9)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=4)   # waves 4, 4, 1
+    xh = np.zeros((9, prob.n_dof))
+    status, st = ctx.pcg(mu9, xh)
+    assert status == rb.RB_OK
+    xd = torch.zeros((9, prob.n_dof), dtype=torch.float64, device="cuda")
+    ctx.pcg(mu9, xd)
+    xd2 = torch.zeros_like(xd)
+    ctx.pcg(mu9, xd2)
+    assert torch.equal(xd, xd2), "two identical solves differ"
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())
+    for b in (0, 5, 8):
+        assert _rel(xh[b], direct.sparse_direct(prob, mu9[b])) < 1e-9
+    # an empty batch is a no-op
+    status, st = ctx.pcg(np.zeros((0, prob.n_mu)), xh[:0])
+    assert status == rb.RB_OK and len(st) == 0
+    ctx.close()
+
+
+def test_no_basis_and_given_start(case2d):
+    w, basis, mu, truth, _ = case2d
+    prob = w.problem
+    ctx0 = rb.Context.from_arrays(prob, np.zeros((prob.n_dof, 0)), np.zeros((prob.P, 0, 0)),
+                                  np.zeros((len(prob.loads), 0)), max_batch=2)
+    x = torch.zeros((2, prob.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx0.pcg(mu[:2], x)
+    assert status == rb.RB_OK
+    for b in range(2):
+        ref = orb.rbcg(orb.Basis(prob, np.zeros((prob.n_dof, 0)), np.zeros((prob.P, 0, 0)),
+                                 np.zeros((len(prob.loads), 0))), mu[b], tol=1e-10, beta="pr")
+        assert _rel(x[b].cpu().numpy(), truth[b]) < 1e-9
+        assert abs(int(st["iters"][b]) - ref.iters) <= 2
+    ctx0.close()
+    # a start close to the solution needs far fewer iterations
+    _, _, _, _, ctx = case2d
+    x0 = truth[:2] * (1 + 1e-6)
+    xg = _dev(x0)
+    status, st2 = ctx.pcg(mu[:2], xg, x0=True)
+    assert status == rb.RB_OK
+    xz = torch.zeros_like(xg)
+    _, st1 = ctx.pcg(mu[:2], xz)
+    assert np.all(st2["iters"] < st1["iters"])
+    for b in range(2):
+        assert _rel(xg[b].cpu().numpy(), truth[b]) < 1e-9
+
+
+def test_error_statuses(case2d):
+    w, basis, mu, truth, ctx = case2d
+    x = torch.zeros((2, w.problem.n_dof), dtype=torch.float64, device="cuda")
+    bad = mu[:2].copy()
+    bad[1, 0] = np.nan
+    with pytest.raises(rb.RbError) as e:
+        ctx.pcg(bad, x)
+    assert e.value.status == rb.RB_EINVAL
+    status, st = ctx.pcg(mu[:2], x, max_iter=3)
+    assert status == rb.RB_ENOCONV and np.all(st["status"] == rb.RB_ENOCONV) and np.all(st["iters"] <= 3)
+    neg = -mu[:2]
+    status, st = ctx.pcg(neg, x)
+    assert status == rb.RB_EBREAKDOWN and np.all(st["status"] == rb.RB_EBREAKDOWN)
+    status, st = ctx.solve(neg, x)
+    assert np.all(st["status"] == rb.RB_EBREAKDOWN)
+    # the context stays usable after the failures
+    status, st = ctx.pcg(mu[:2], x)
+    assert status == rb.RB_OK
+
+
+@pytest.mark.parametrize("dims", [(128, 40), (256, 33)])
+def test_rowmarch_2d_matches_oracle(dims):
+    """Grids whose width is a multiple of 128 take the row-marching kernels (bands of 32 rows,
+    the last one ragged): same FP64 iterations as the oracle replica, mixed reaches truth."""
+    w = wl.small(dims, (3, 2), n_basis=6, n_train=24, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu, x, precision="fp64")
+    assert status == rb.RB_OK
+    for b in range(3):
+        ref = orb.rbcg(basis, mu[b], tol=1e-10, beta="pr")
+        assert abs(int(st["iters"][b]) - ref.iters) <= 2, (st[b], ref.iters)
+        assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9
+    for nu in (1, 2):
+        x.zero_()
+        status, st = ctx.pcg(mu, x, precision="mixed", nu=nu)
+        assert status == rb.RB_OK
+        for b in range(3):
+            assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9
+    x.zero_()
+    status, st = ctx.pcg(mu, x, precision="fp64", nu=2)
+    for b in range(3):
+        ref = orb.rbcg(basis, mu[b], tol=1e-10, beta="pr", nu=2)
+        assert abs(int(st["iters"][b]) - ref.iters) <= 2, (st[b], ref.iters)
+    ctx.close()
+
+
+def test_3d_fp64_and_mixed():
+    w = wl.small((14, 12, 10), (2, 2, 2), n_basis=6, n_train=24)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    for precision in ("fp64", "mixed"):
+        x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+        status, st = ctx.pcg(mu, x, precision=precision)
+        assert status == rb.RB_OK
+        for b in range(3):
+            assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9
+    x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.solve(mu, x)
+    assert status == rb.RB_OK
+    for b in range(3):
+        ref = orb.rbi(basis, mu[b], tol=1e-10)
+        assert abs(int(st["iters"][b]) - ref.iters) <= 2
+    ctx.close()
+
+
+def test_offline_build_matches_oracle_greedy():
+    w = wl.small((24, 20), (2, 2), n_basis=5, n_train=30, bumps=True)
+    prob = w.problem
+    ref = greedy.greedy(prob, w.train_mu(), 5)
+    ctx = rb.Context.build(prob, 5, w.train_mu(), max_batch=2)
+    W, ANq, fNr, Rs, sel = ctx.basis()
+    assert list(sel) == list(ref.selected)
+    assert np.abs(W.T @ W - np.eye(5)).max() < 1e-12
+    signs = np.sign(np.sum(W * ref.W, axis=0))
+    assert np.abs(W * signs - ref.W).max() < 1e-8
+    S = np.diag(signs)
+    for q in range(prob.P):
+        assert np.abs(S @ ANq[q] @ S - ref.ANq[q]).max() < 1e-8 * np.abs(ref.ANq[q]).max()
+    np.testing.assert_allclose(fNr * signs, ref.fNr, rtol=1e-8, atol=1e-12)
+    # the snapshot factor reproduces the oracle's (up to the same column signs)
+    np.testing.assert_allclose(S @ Rs, ref.R, rtol=1e-7, atol=1e-9 * np.abs(ref.R).max())
+    ctx.close()
+
+
+def test_save_load_roundtrip_and_corruption(case2d):
+    w, basis, mu, truth, ctx = case2d
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "b.rbb")
+        ctx.save(path)
+        c2 = rb.Context.load(path, max_batch=2)
+        W, ANq, fNr, _, _ = c2.basis()
+        np.testing.assert_array_equal(W, basis.W)
+        np.testing.assert_array_equal(ANq, basis.ANq)
+        x = torch.zeros((2, w.problem.n_dof), dtype=torch.float64, device="cuda")
+        status, _ = c2.pcg(mu[:2], x)
+        assert status == rb.RB_OK and _rel(x[0].cpu().numpy(), truth[0]) < 1e-9
+        c2.close()
+        raw = bytearray(open(path, "rb").read())
+        raw[200] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(rb.RbError) as e:
+            rb.Context.load(path)
+        assert e.value.status == rb.RB_EFORMAT
+        open(path, "wb").write(bytes(raw[:1000]))
+        with pytest.raises(rb.RbError) as e:
+            rb.Context.load(path)
+        assert e.value.status == rb.RB_EFORMAT
+        with pytest.raises(rb.RbError) as e:
+            rb.Context.load(os.path.join(d, "missing.rbb"))
+        assert e.value.status == rb.RB_EIO
