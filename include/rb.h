@@ -181,6 +181,29 @@ typedef struct {
 rb_status rb_profile(rb_ctx* ctx, int enable);
 rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* count);
 
+/*
+ * Relative residuals rel_res[b] = ||f(mu_b) - A(mu_b) x_b|| / ||f(mu_b)|| (FP64)
+ * of a batch of device vectors, computed WITHOUT ALLOCATING device memory.
+ * The paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc, such as code running under a framework whose caching allocator
+ * holds the device memory, or latency-bound code that cannot accept the
+ * device-wide synchronisation an allocation may cause.  It needs no rb_ctx.
+ *   prob     the problem, as for rb_offline_load_arrays;
+ *   mu       host [B][n_mu];   x  device [B][N_dof] (host memory is rejected);
+ *   rel_res  host [B], written; stream as in rb_opts (may be NULL).
+ * Scratch: one static 1 MiB device array per GPU that loads the library, held
+ * until the process exits.  It must hold B*n_mu + 2*B*ceil(N_dof/1024) + B
+ * doubles (each part rounded up to 256 bytes); a larger batch is rejected with
+ * RB_EINVAL and a message in rb_last_error(NULL).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the array and overwrites what it reads, so calls that overlap on the GPU
+ * (other threads or streams) race: serialise them.  Synchronous: returns after
+ * rel_res is on the host.
+ */
+rb_status rb_residual_noalloc(const rb_problem* prob, int B, const double* mu, const double* x,
+                              double* rel_res, void* stream);
+
 /* Text of the last error on ctx (or of the last failed context creation when
  * ctx is NULL).  Valid until the next call on that context. */
 const char* rb_last_error(const rb_ctx* ctx);

@@ -24,6 +24,11 @@ struct DevBuf {
 
 }  // namespace
 
+namespace rbk {
+// error text of calls that have no context (read back by rb_last_error(NULL))
+void set_global_error(const std::string& m) { g_create_error = m; }
+}  // namespace rbk
+
 struct rb_ctx {
     // problem
     int dim = 2, m[3] = {1, 1, 1}, nbk[3] = {1, 1, 1}, P = 1, R = 1, n_mu = 1;

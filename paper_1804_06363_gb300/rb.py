@@ -74,6 +74,8 @@ SIGNATURES = {
     "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
+    "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "rb_last_error": (C.c_char_p, [C.c_void_p]),
     "rb_status_string": (C.c_char_p, [C.c_int]),
     "rb_free": (None, [C.c_void_p]),
@@ -175,6 +177,18 @@ def stats_array(st) -> np.ndarray:
                              ("rel_res", "f8")])
     for i in range(n):
         out[i] = (st[i].iters, st[i].outer, st[i].restarts, st[i].status, st[i].rel_res)
+    return out
+
+
+def residual_noalloc(prob, mu, x, stream: Optional[int] = None) -> np.ndarray:
+    """rb_residual_noalloc: relative residuals of device vectors x [B][N_dof], no device allocation."""
+    p, keep = make_problem(prob)
+    mu = _f64(mu).reshape(-1, prob.n_mu)
+    out = np.zeros(mu.shape[0])
+    st = lib().rb_residual_noalloc(C.byref(p), mu.shape[0], _ptr(mu), _ptr(x), _ptr(out),
+                                   C.c_void_p(int(stream) if stream else 0))
+    if st != RB_OK:
+        raise RbError(st, lib().rb_last_error(None).decode())
     return out
 
 
