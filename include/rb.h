@@ -162,6 +162,16 @@ rb_status rb_solve(rb_ctx* ctx, int B, const double* mu, double* x,
 rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x,
                  const rb_opts* opts, rb_stats* stats);
 
+/* The two batched products of the RB preconditioner in FP32 storage, with the
+ * engine of the mixed path: WtR[b] = W^T R[b] (eq. 5, as in Alg. 2 step 4) and
+ * WE[b] = W E[b] (eq. 7, as in Alg. 2 step 6).  engine: RB_GEMM_CUDA_CORES
+ * (FP32 FMA), RB_GEMM_TENSOR (tcgen05 with TF32 operands, FP32 accumulation;
+ * RB_EINVAL where unavailable) or RB_GEMM_AUTO.  R host or device [B][N_dof]
+ * float, WtR host [B][n] double; E host [B][n] float, WE host or device
+ * [B][N_dof] float.  Either pair may be NULL.  B <= max_batch.  Uses the
+ * context's workspace (overwrites solver state; not during a solve). */
+rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const float* E, float* WE, int engine);
+
 /* y = A(mu_b) x_b for every query b (eq. 1 operator, FP64).  x, y host or device
  * [B][N_dof]; stream as in rb_opts (may be NULL). */
 rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y,

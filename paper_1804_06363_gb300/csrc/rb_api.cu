@@ -69,6 +69,8 @@ struct rb_ctx {
     double* d_scratch = nullptr;      // offline helpers
     size_t scratch_bytes = 0;
     TcPlan tc{};                      // tensor-core projection plans
+    int* d_tcerr = nullptr;           // set by a tensor-core kernel whose wait expired
+    int nsplit_max = 1;
     bool force_generic = false;       // testing: use the generic stencil kernels everywhere
     // per-kernel timing (rb_profile)
     bool profiling = false;
@@ -238,12 +240,12 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     // batch workspace
     const size_t BN = (size_t)B * N;
     TRY(dalloc(ctx, &ctx->d_x64, BN));
-    TRY(dalloc(ctx, &ctx->d_r64, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_r64, BN));
     TRY(dalloc(ctx, &ctx->d_p64, 2 * BN));
     TRY(dalloc(ctx, &ctx->d_y64, BN));
     TRY(dalloc(ctx, &ctx->d_ypro64, BN));
     TRY(dalloc(ctx, &ctx->d_tmp64, BN));
-    TRY(dalloc(ctx, &ctx->d_r32, 2 * BN));
+    TRY(dalloc(ctx, &ctx->d_r32, BN));
     TRY(dalloc(ctx, &ctx->d_p32, 2 * BN));
     TRY(dalloc(ctx, &ctx->d_y32, BN));
     TRY(dalloc(ctx, &ctx->d_ypro32, BN));
@@ -251,8 +253,8 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     TRY(dalloc(ctx, &ctx->d_d32, BN));
     CK(cudaMemset(ctx->d_p64, 0, 2 * BN * sizeof(double)));
     CK(cudaMemset(ctx->d_p32, 0, 2 * BN * sizeof(float)));
-    CK(cudaMemset(ctx->d_r64, 0, 2 * BN * sizeof(double)));
-    CK(cudaMemset(ctx->d_r32, 0, 2 * BN * sizeof(float)));
+    CK(cudaMemset(ctx->d_r64, 0, BN * sizeof(double)));
+    CK(cudaMemset(ctx->d_r32, 0, BN * sizeof(float)));
     TRY(dalloc(ctx, &ctx->d_e64, (size_t)B * nbp));
     TRY(dalloc(ctx, &ctx->d_e32, (size_t)B * ctx->nbp32));
     CK(cudaMemset(ctx->d_e32, 0, (size_t)B * ctx->nbp32 * sizeof(float)));
@@ -262,7 +264,8 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     ctx->max_tiles = std::max(tiles_flat(N), tiles_box(g));
     TRY(dalloc(ctx, &ctx->d_part, (size_t)B * ctx->max_tiles * 4));
     ctx->nsplit = (int)std::max<long long>(1, std::min<long long>(64, N / 4096));
-    TRY(dalloc(ctx, &ctx->d_proj, (size_t)ctx->nsplit * B * nbp));
+    ctx->nsplit_max = std::max(ctx->nsplit, ctx->num_sms);
+    TRY(dalloc(ctx, &ctx->d_proj, (size_t)ctx->nsplit_max * B * nbp));
     TRY(dalloc(ctx, &ctx->d_tick, B));
     CK(cudaMemset(ctx->d_tick, 0, B * sizeof(unsigned)));
     TRY(dalloc(ctx, &ctx->d_lcnt, N_LISTS));
@@ -270,7 +273,10 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     TRY(dalloc(ctx, &ctx->d_ndone, 1));
     ctx->scratch_bytes = std::max<size_t>((size_t)128 * 128 * 128 * sizeof(double), 4096);
     TRY(dalloc(ctx, &ctx->d_scratch, ctx->scratch_bytes / sizeof(double)));
-    TRY(tc_init(ctx->tc, ctx->geo, B, ctx->nbp32, ctx->num_sms, ctx->err));
+    TRY(dalloc(ctx, &ctx->d_tcerr, 1));
+    CK(cudaMemset(ctx->d_tcerr, 0, sizeof(int)));
+    TRY(tc_init(ctx->tc, ctx->geo, B, n_cap, nbp, ctx->nbp32, ctx->num_sms, ctx->d_r32, ctx->d_W32c, ctx->d_e32,
+                ctx->d_W32r, ctx->d_tcerr, ctx->err));
 
     if (cudaMallocHost((void**)&ctx->h_st, (size_t)B * sizeof(QState)) != cudaSuccess ||
         cudaMallocHost((void**)&ctx->h_ndone, sizeof(int)) != cudaSuccess) {
@@ -364,7 +370,7 @@ struct Mode {
     bool mixed;
 };
 
-Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m) {
+Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bool use_tc) {
     Params P{};
     P.g = ctx->geo;
     P.B = B;
@@ -391,7 +397,8 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m) {
     P.part = ctx->d_part;
     P.max_tiles = ctx->max_tiles;
     P.proj = ctx->d_proj;
-    P.nsplit = ctx->nsplit;
+    P.nsplit = use_tc ? ctx->tc.proj_split : ctx->nsplit;
+    P.lde = (m.mixed && use_tc) ? ctx->nbp32 : ctx->nbp;
     P.tick = ctx->d_tick;
     P.lcnt = ctx->d_lcnt;
     P.lidx = ctx->d_lidx;
@@ -474,7 +481,7 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
         if (use_tc) {
             timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
             timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
-            timed(ctx, KK_TC_PROLONG, s, [&] { tc_prolong(ctx->tc, P, L, ctx->d_W32r); });
+            timed(ctx, KK_TC_PROLONG, s, [&] { tc_prolong(ctx->tc, P, L); });
         } else {
             timed(ctx, KK_PROJECT, s, [&] { launch_project<float>(P, L); });
             timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
@@ -545,12 +552,15 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
     if (!x_given) CK(cudaMemsetAsync(x64, 0, (size_t)B * N * sizeof(double), s));
     if (m.mixed) CK(cudaMemsetAsync(ctx->d_d32, 0, (size_t)B * N * sizeof(float), s));
 
-    Params P = make_params(ctx, B, x64, o, m);
+    const bool use_tc = m.mixed && o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
+    if (m.mixed && o.gemm == RB_GEMM_TENSOR && !use_tc) {
+        ctx->err = "tensor-core engine unavailable for this problem (needs N_dof % 32 == 0, n >= 1, sm_10x)";
+        return RB_EINVAL;
+    }
+    Params P = make_params(ctx, B, x64, o, m, use_tc);
     Launch L{ctx->grid, s};
     launch_cholesky(P, s, ctx->d_ANq, ctx->P);
     CK(cudaGetLastError());
-
-    const bool use_tc = m.mixed && o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
     const int check_every = 8;
     cudaGraphExec_t exec = nullptr;
     if (o.graph && s != nullptr && !ctx->profiling) {
@@ -593,6 +603,16 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (rs != RB_OK) return rs;
+    if (use_tc) {
+        int tcerr = 0;
+        CK(cudaMemcpyAsync(&tcerr, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (tcerr) {
+            cudaMemsetAsync(ctx->d_tcerr, 0, sizeof(int), s);
+            ctx->err = "a tensor-core kernel gave up waiting on its pipeline (device timeout)";
+            return RB_ETIMEOUT;
+        }
+    }
     CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, (size_t)B * sizeof(QState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     rb_status worst = RB_OK;
@@ -749,6 +769,68 @@ rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* 
         ++c;
     }
     if (count) *count = c;
+    return RB_OK;
+}
+
+rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const float* E, float* WE, int engine) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || B > ctx->Bmax) { ctx->err = "need 0 <= B <= max_batch"; return RB_EINVAL; }
+    if (B == 0) return RB_OK;
+    const int n = ctx->n;
+    if (n == 0) { ctx->err = "the context has no basis"; return RB_EINVAL; }
+    const bool can_tc = tc_usable(ctx->tc, n);
+    if (engine == RB_GEMM_TENSOR && !can_tc) { ctx->err = "tensor-core engine unavailable for this problem"; return RB_EINVAL; }
+    const bool use_tc = engine == RB_GEMM_TENSOR || (engine == RB_GEMM_AUTO && can_tc);
+    rb_opts o;
+    rb_default_opts(&o);
+    o.precision = RB_PREC_MIXED;
+    cudaStream_t s = ctx->own_stream;
+    const long long N = ctx->N;
+    Params P = make_params(ctx, B, ctx->d_x64, o, Mode{false, true}, use_tc);
+    Launch L{ctx->grid, s};
+    for (int q = 0; q < B; ++q) {
+        std::memset(&ctx->h_st[q], 0, sizeof(QState));
+        ctx->h_st[q].phase = PH_PREC;
+    }
+    CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
+    std::vector<int> lc(N_LISTS, 0), li(B);
+    lc[L_PREC] = B;
+    for (int q = 0; q < B; ++q) li[q] = q;
+    CK(cudaMemcpyAsync(ctx->d_lcnt, lc.data(), N_LISTS * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lidx + L_PREC * ctx->Bmax, li.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (R && WtR) {
+        CK(cudaMemcpyAsync(ctx->d_r32, R, (size_t)B * N * sizeof(float), cudaMemcpyDefault, s));
+        if (use_tc) tc_project(ctx->tc, P, L);
+        else launch_project<float>(P, L);
+        CK(cudaGetLastError());
+        std::vector<double> part((size_t)P.nsplit * ctx->Bmax * ctx->nbp);
+        CK(cudaMemcpyAsync(part.data(), ctx->d_proj, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int q = 0; q < B; ++q)
+            for (int k = 0; k < n; ++k) {
+                double acc = 0.0;
+                for (int sp = 0; sp < P.nsplit; ++sp) acc += part[((size_t)sp * ctx->Bmax + q) * ctx->nbp + k];
+                WtR[(size_t)q * n + k] = acc;
+            }
+    }
+    if (E && WE) {
+        std::vector<float> e((size_t)B * P.lde, 0.0f);
+        for (int q = 0; q < B; ++q)
+            for (int k = 0; k < n; ++k) e[(size_t)q * P.lde + k] = E[(size_t)q * n + k];
+        CK(cudaMemcpyAsync(ctx->d_e32, e.data(), e.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (use_tc) tc_prolong(ctx->tc, P, L);
+        else launch_prolong<float>(P, L, false);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(WE, ctx->d_ypro32, (size_t)B * N * sizeof(float), cudaMemcpyDefault, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    int tcerr = 0;
+    CK(cudaMemcpy(&tcerr, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tcerr) {
+        cudaMemset(ctx->d_tcerr, 0, sizeof(int));
+        ctx->err = "a tensor-core kernel gave up waiting on its pipeline (device timeout)";
+        return RB_ETIMEOUT;
+    }
     return RB_OK;
 }
 

@@ -5,9 +5,10 @@
 //   W32c  [nbp][N]   FP32 copy (K-major operand of the batched projection)
 //   W32r  [N][nbp32] FP32 copy, row-major (K-major operand of the prolongation)
 //   fr    [R][N]     FP64 load terms f_r (eq. 12)
-//   batch vectors [B][N] per buffer, query-major, x fastest; residual and
-//   search direction are ping-ponged ([2][B][N]) so that a stencil kernel never
-//   reads a neighbour that another CTA of the same launch has already rewritten.
+//   batch vectors [B][N] per buffer, query-major, x fastest.  The search
+//   direction is ping-ponged ([2][B][N]): the kernel that rebuilds it reads its
+//   neighbours, which another CTA of the same launch may already have
+//   rewritten.  The residual is updated in place (only point-wise reads).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,7 +57,8 @@ struct QState {
     int iters, outer, restarts, status;
     int phase;
     int start;           // 1: the next preconditioner output starts a CG cycle (beta = 0)
-    int rpar, ppar;      // current halves of the r and p ping-pong buffers
+    int ppar;            // current half of the p ping-pong buffer
+    int rpar_unused;
     int xzero;           // x is exactly zero (skip A x in the residual)
     int pad_;
 };
@@ -78,13 +80,14 @@ struct Params {
     const double* L;             // [Bmax][nbp][nbp] Cholesky factors (lower, row-major)
     // vectors
     double* x64;                 // [B][N] FP64 iterate / solution
-    void* r;                     // [2][B][N] of T
+    void* r;                     // [B][N] of T (updated in place)
     void* p;                     // [2][B][N] of T
     void* y;                     // [B][N] of T
     void* ypro;                  // [B][N] of T
     void* tmp;                   // [B][N] of T (smoother ping-pong for nu >= 2)
     void* d;                     // [B][N] of T: inner iterate (aliases x64 in FP64 mode)
-    void* e;                     // [B][nbp] of T: reduced correction e_N
+    void* e;                     // [B][lde] of T: reduced correction e_N (zero beyond nb)
+    int lde;
     // reductions and lists
     QState* st;
     double* part;                // [B][max_tiles][4]

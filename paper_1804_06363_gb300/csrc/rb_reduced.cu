@@ -11,7 +11,7 @@ constexpr int PC = 32;     // points per shared-memory chunk of the projection
 
 template <typename T>
 __device__ __forceinline__ const T* cur_r(const Params& P, int q) {
-    return reinterpret_cast<const T*>(P.r) + ((size_t)q * 2 + P.st[q].rpar) * (size_t)P.g.n;
+    return reinterpret_cast<const T*>(P.r) + (size_t)q * (size_t)P.g.n;
 }
 
 template <typename T> __device__ __forceinline__ const T* basis_c(const Params& P);
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(THREADS) k_reduced_solve(Params P) {
             for (int k = lane; k < i; k += 32) v[k] -= L[(size_t)i * nbp + k] * ei;
             __syncwarp();
         }
-        T* e = reinterpret_cast<T*>(P.e) + (size_t)q * nbp;
-        for (int k = lane; k < nbp; k += 32) e[k] = k < nb ? (T)v[k] : T(0);
+        T* e = reinterpret_cast<T*>(P.e) + (size_t)q * P.lde;
+        for (int k = lane; k < P.lde; k += 32) e[k] = k < nb ? (T)v[k] : T(0);
         __syncwarp();
     }
 }
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(THREADS) k_prolong(Params P) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < PG * nb; idx += THREADS) {
             const int gq = idx / nb, k = idx % nb;
-            es[gq][k] = qs[gq] >= 0 ? reinterpret_cast<const T*>(P.e)[(size_t)qs[gq] * nbp + k] : T(0);
+            es[gq][k] = qs[gq] >= 0 ? reinterpret_cast<const T*>(P.e)[(size_t)qs[gq] * P.lde + k] : T(0);
         }
         __syncthreads();
 #pragma unroll

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(THREADS) k_outer_residual(Params P) {
         load_mu(P, q, mus);
         const QState& s = P.st[q];
         const int xzero = s.xzero;
-        T* rout = vec<T>(P.r, P, q, s.rpar);
+        T* rout = vec1<T>(P.r, P, q);
         const double* x = P.x64 + (size_t)q * P.g.n;
         double rr = 0.0, ff = 0.0;
 #pragma unroll
@@ -230,7 +230,6 @@ __device__ void finalize_cg_b(const Params& P, int q, double rr) {
     const double rn = sqrt(rr);
     s.rnorm = rn;
     s.iters += 1;
-    s.rpar ^= 1;
     if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
     if (rn < s.target || s.iters >= P.max_iter) {
         s.phase = PH_OUTER;
@@ -256,8 +255,7 @@ __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
         load_mu(P, q, mus);
         const T alpha = (T)s.alpha;
         const T* p = vec<T>(P.p, P, q, s.ppar);
-        const T* rold = vec<T>(P.r, P, q, s.rpar);
-        T* rnew = vec<T>(P.r, P, q, s.rpar ^ 1);
+        T* rr = vec1<T>(P.r, P, q);
         T* d = P.mixed ? vec1<T>(P.d, P, q) : reinterpret_cast<T*>(P.x64 + (size_t)q * P.g.n);
         T acc = T(0);
 #pragma unroll
@@ -271,8 +269,8 @@ __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
                 const T pi = p[i];
                 const T api = c.diag * pi - offdiag_sum(P.g, c, i, ix, iy, iz, [&](long long k) { return p[k]; });
                 d[i] += alpha * pi;
-                const T rv = rold[i] - alpha * api;
-                rnew[i] = rv;
+                const T rv = rr[i] - alpha * api;
+                rr[i] = rv;
                 acc += rv * rv;
             }
         }
@@ -302,14 +300,16 @@ __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
 
 enum { SM_NONE = 0, SM_RBGS = 1, SM_JACOBI = 2 };
 
-__device__ void finalize_prec(const Params& P, int q, double ry, double roy) {
+// ry = r_{k+1}^T y_{k+1}; apy = (A p_k)^T y_{k+1}.  Polak-Ribiere:
+// y_{k+1}^T (r_{k+1} - r_k) = -alpha_k (A p_k)^T y_{k+1} since r_{k+1} = r_k - alpha_k A p_k.
+__device__ void finalize_prec(const Params& P, int q, double ry, double apy) {
     QState& s = P.st[q];
     if (!(ry > 0.0)) { mark_done(P, s, RB_EBREAKDOWN); return; }
     if (s.start) {
         s.beta = 0.0;
         s.start = 0;
     } else {
-        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : (ry - roy) / s.rho;
+        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : -s.alpha * apy / s.rho;
     }
     s.rho = ry;
     s.phase = PH_ITER;
@@ -346,8 +346,10 @@ __global__ void __launch_bounds__(THREADS) k_smooth(Params P, const T* __restric
         const int tz0 = (tile / (ntx * nty)) * BX::Z;
         const T* src = src_base + (size_t)q * g.n;
         T* dst = dst_base + (size_t)q * g.n;
-        const T* bT = RBI ? nullptr : vec<T>(P.r, P, q, s.rpar);
-        const T* rold = RBI ? nullptr : vec<T>(P.r, P, q, s.rpar ^ 1);
+        const T* bT = RBI ? nullptr : vec1<T>(P.r, P, q);
+        // Polak-Ribiere needs (A p)^T y with the direction p of the step just taken
+        const bool need_ap = !RBI && LAST && P.beta_form == RB_BETA_PR && !s.start;
+        const T* pdir = need_ap ? vec<T>(P.p, P, q, s.ppar) : nullptr;
         auto bval = [&](long long i) -> T {
             if constexpr (RBI) return (T)load_value(P, musd, i);
             else return bT[i];
@@ -408,7 +410,13 @@ __global__ void __launch_bounds__(THREADS) k_smooth(Params P, const T* __restric
                 dst[i] = z;
                 if constexpr (!RBI && LAST) {
                     ry += bT[i] * z;
-                    roy += rold[i] * z;
+                    if (need_ap) {
+                        Coef<T> c;
+                        node_coef(g, mus, ix, iy, iz, c);
+                        const T ap = c.diag * pdir[i] -
+                                     offdiag_sum(g, c, i, ix, iy, iz, [&](long long k) { return pdir[k]; });
+                        roy += ap * z;
+                    }
                 }
             }
         }
@@ -511,7 +519,7 @@ __global__ void __launch_bounds__(THREADS) k_rbi_residual(Params P) {
         load_mu(P, q, mus);
         const QState& s = P.st[q];
         const int xzero = s.xzero;
-        double* rout = vec<double>(P.r, P, q, 0);
+        double* rout = vec1<double>(P.r, P, q);
         const double* x = P.x64 + (size_t)q * P.g.n;
         double rr = 0.0, ff = 0.0;
 #pragma unroll

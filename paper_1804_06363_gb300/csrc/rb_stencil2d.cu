@@ -144,7 +144,6 @@ __device__ void finalize_cg_b2(const Params& P, int q, double rr) {
     const double rn = sqrt(rr);
     s.rnorm = rn;
     s.iters += 1;
-    s.rpar ^= 1;
     if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
     if (rn < s.target || s.iters >= P.max_iter) {
         s.phase = PH_OUTER;
@@ -155,14 +154,15 @@ __device__ void finalize_cg_b2(const Params& P, int q, double rr) {
     }
 }
 
-__device__ void finalize_prec2(const Params& P, int q, double ry, double roy) {
+// Polak-Ribiere: y_{k+1}^T (r_{k+1} - r_k) = -alpha_k (A p_k)^T y_{k+1}
+__device__ void finalize_prec2(const Params& P, int q, double ry, double apy) {
     QState& s = P.st[q];
     if (!(ry > 0.0)) { mark_done(P, s, RB_EBREAKDOWN); return; }
     if (s.start) {
         s.beta = 0.0;
         s.start = 0;
     } else {
-        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : (ry - roy) / s.rho;
+        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : -s.alpha * apy / s.rho;
     }
     s.rho = ry;
     s.phase = PH_ITER;
@@ -272,8 +272,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
         const T alpha = (T)s.alpha;
         const size_t base = (size_t)q * g.n;
         const T* p = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n + x0;
-        const T* ro = reinterpret_cast<const T*>(P.r) + ((size_t)q * 2 + s.rpar) * g.n + x0;
-        T* rn = reinterpret_cast<T*>(P.r) + ((size_t)q * 2 + (s.rpar ^ 1)) * g.n + x0;
+        T* rr = reinterpret_cast<T*>(P.r) + base + x0;
         T* d = (P.mixed ? reinterpret_cast<T*>(P.d) : reinterpret_cast<T*>(P.x64)) + base + x0;
         auto prow = [&](int k) -> V4<T> { return (k < 0 || k >= my) ? zero4<T>() : ld4k(p + (size_t)k * mx); };
         const int y0 = band * RB_ROWS, y1 = min(my, y0 + RB_ROWS);
@@ -283,7 +282,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
         for (int k = y0; k < y1; ++k) {
             const V4<T> vp = prow(k + 1);
             const V4<T> dk = ld4(d + (size_t)k * mx);
-            const V4<T> rk = ld4(ro + (size_t)k * mx);
+            const V4<T> rk = ld4(rr + (size_t)k * mx);
             T left, right;
             xhalo(vc, sx, sw, buf, nwarps, left, right);
             buf ^= 1;
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
                 acc += rnew.v[j] * rnew.v[j];
             }
             st4(d + (size_t)k * mx, dn);
-            st4(rn + (size_t)k * mx, rnew);
+            st4(rr + (size_t)k * mx, rnew);
             vm = vc;
             vc = vp;
         }
@@ -327,7 +326,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
 template <typename T, bool LAST>
 __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
     __shared__ T mus[MAX_MU];
-    __shared__ T sx[64], sw[64], sx2[64], sw2[64];
+    __shared__ T sx[3][64], sw[3][64];
     __shared__ double red[32];
     const Geo& g = P.g;
     const int mx = g.mx, my = g.my;
@@ -338,6 +337,7 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
     const long long total = (long long)cnt * nband;
     ColMap<T> cm;
     col_map(g, x0, cm);
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     // colour of point j of row k: (x0 + j + k) & 1, x0 even: (j + k) & 1
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / nband), band = (int)(w % nband);
@@ -349,44 +349,50 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
         const size_t base = (size_t)q * g.n;
         const T* src = src_base + base + x0;
         T* dst = dst_base + base + x0;
-        const T* r = reinterpret_cast<const T*>(P.r) + ((size_t)q * 2 + s.rpar) * g.n + x0;
-        const T* ro = reinterpret_cast<const T*>(P.r) + ((size_t)q * 2 + (s.rpar ^ 1)) * g.n + x0;
+        const T* r = reinterpret_cast<const T*>(P.r) + base + x0;
+        // Polak-Ribiere needs (A p)^T y with the direction p of the step just taken
+        const bool need_ap = LAST && P.beta_form == RB_BETA_PR && !s.start;
+        const T* pd = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n + x0;
         auto srow = [&](int k) -> V4<T> { return (k < 0 || k >= my) ? zero4<T>() : ld4k(src + (size_t)k * mx); };
         auto rrow = [&](int k) -> V4<T> { return (k < 0 || k >= my) ? zero4<T>() : ld4k(r + (size_t)k * mx); };
+        auto prow = [&](int k) -> V4<T> {
+            return (!need_ap || k < 0 || k >= my) ? zero4<T>() : ld4k(pd + (size_t)k * mx);
+        };
         const int y0 = band * RB_ROWS, y1 = min(my, y0 + RB_ROWS);
-        // src rows k-1, k, k+1 around the red row k; new red rows k-2, k-1, k; r rows k-1, k
+        // src rows k-1, k, k+1 around the red row k; new red rows k-2, k-1, k; r row k-1;
+        // p rows k-2, k-1, k around the black row k-1
         V4<T> sm = srow(y0 - 2), sc = srow(y0 - 1);
-        V4<T> zm = zero4<T>(), zc = zero4<T>();     // new red values, rows k-2, k-1
-        V4<T> rc = zero4<T>();                        // r row k-1
-        RowCoef<T> cprev;                             // coefficients of row k-1
-        T ry = T(0), roy = T(0);
+        V4<T> zm = zero4<T>(), zc = zero4<T>();
+        V4<T> rc = zero4<T>();
+        V4<T> pm = zero4<T>(), pc = zero4<T>();
+        RowCoef<T> cprev;
+        T ry = T(0), apy = T(0);
         int buf = 0;
         for (int k = y0 - 1; k <= y1; ++k) {
             const V4<T> sp = srow(k + 1);
             const V4<T> rk = rrow(k);
-            // one exchange for the src row k (red update) and the new red row k-1 (black update)
-            T sl, sr, zl, zr;
-            {
-                const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-                sl = __shfl_up_sync(0xffffffffu, sc.v[3], 1);
-                sr = __shfl_down_sync(0xffffffffu, sc.v[0], 1);
-                zl = __shfl_up_sync(0xffffffffu, zc.v[3], 1);
-                zr = __shfl_down_sync(0xffffffffu, zc.v[0], 1);
-                if (lane == 31) { sw[buf * 32 + wi] = sc.v[3]; sw2[buf * 32 + wi] = zc.v[3]; }
-                if (lane == 0) { sx[buf * 32 + wi] = sc.v[0]; sx2[buf * 32 + wi] = zc.v[0]; }
-                __syncthreads();
-                if (lane == 0) {
-                    sl = wi > 0 ? sw[buf * 32 + wi - 1] : T(0);
-                    zl = wi > 0 ? sw2[buf * 32 + wi - 1] : T(0);
-                }
-                if (lane == 31) {
-                    sr = wi + 1 < nwarps ? sx[buf * 32 + wi + 1] : T(0);
-                    zr = wi + 1 < nwarps ? sx2[buf * 32 + wi + 1] : T(0);
-                }
-                buf ^= 1;
-                if (!cm.left) { sl = T(0); zl = T(0); }
-                if (!cm.right) { sr = T(0); zr = T(0); }
+            const V4<T> pk = prow(k);
+            // one exchange for the src row k (red update), the new red row k-1 (black
+            // update) and the direction row k-1 (A p at the black row)
+            T v0[3] = {sc.v[0], zc.v[0], pc.v[0]};
+            T v3[3] = {sc.v[3], zc.v[3], pc.v[3]};
+            T lft[3], rgt[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                lft[t] = __shfl_up_sync(0xffffffffu, v3[t], 1);
+                rgt[t] = __shfl_down_sync(0xffffffffu, v0[t], 1);
+                if (lane == 31) sw[t][buf * 32 + wi] = v3[t];
+                if (lane == 0) sx[t][buf * 32 + wi] = v0[t];
             }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (lane == 0) lft[t] = wi > 0 ? sw[t][buf * 32 + wi - 1] : T(0);
+                if (lane == 31) rgt[t] = wi + 1 < nwarps ? sx[t][buf * 32 + wi + 1] : T(0);
+                if (!cm.left) lft[t] = T(0);
+                if (!cm.right) rgt[t] = T(0);
+            }
+            buf ^= 1;
             // red half-sweep on row k (inside the grid)
             V4<T> zk = zero4<T>();
             RowCoef<T> ck;
@@ -395,8 +401,8 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (((j + k) & 1) == 0) {
-                        const T xl = j == 0 ? sl : sc.v[j - 1];
-                        const T xr = j == 3 ? sr : sc.v[j + 1];
+                        const T xl = j == 0 ? lft[0] : sc.v[j - 1];
+                        const T xr = j == 3 ? rgt[0] : sc.v[j + 1];
                         const T num = rk.v[j] + ck.kx[j] * xl + ck.kx[j + 1] * xr + ck.kym[j] * sm.v[j] +
                                       ck.kyp[j] * sp.v[j];
                         zk.v[j] = num / ck.diag[j];
@@ -412,8 +418,8 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
                     if (((j + kb) & 1) == 0) {
                         out.v[j] = zc.v[j];
                     } else {
-                        const T xl = j == 0 ? zl : zc.v[j - 1];
-                        const T xr = j == 3 ? zr : zc.v[j + 1];
+                        const T xl = j == 0 ? lft[1] : zc.v[j - 1];
+                        const T xr = j == 3 ? rgt[1] : zc.v[j + 1];
                         const T num = rc.v[j] + cprev.kx[j] * xl + cprev.kx[j + 1] * xr + cprev.kym[j] * zm.v[j] +
                                       cprev.kyp[j] * zk.v[j];
                         out.v[j] = num / cprev.diag[j];
@@ -421,11 +427,12 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
                 }
                 st4(dst + (size_t)kb * mx, out);
                 if (LAST) {
-                    const V4<T> rold = ld4(ro + (size_t)kb * mx);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        ry += rc.v[j] * out.v[j];
-                        roy += rold.v[j] * out.v[j];
+                    for (int j = 0; j < 4; ++j) ry += rc.v[j] * out.v[j];
+                    if (need_ap) {
+                        const V4<T> ap = apply_row(cprev, pm, pc, pk, lft[2], rgt[2]);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) apy += ap.v[j] * out.v[j];
                     }
                 }
             }
@@ -434,12 +441,14 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
             zm = zc;
             zc = zk;
             rc = rk;
+            pm = pc;
+            pc = pk;
             cprev = ck;
         }
         if (LAST) {
             double v[2];
             v[0] = block_sum2d(ry, red);
-            v[1] = block_sum2d(roy, red);
+            v[1] = block_sum2d(apy, red);
             if (arrive(P, q, band, nband, v, 2)) {
                 double tot[2];
                 gather_partials(P, q, nband, 2, tot, red);

@@ -72,6 +72,7 @@ SIGNATURES = {
     "rb_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
     "rb_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
     "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_products": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
     "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -280,6 +281,17 @@ class Context:
         mu = _f64(mu).reshape(-1, self.n_mu)
         self._check(lib().rb_apply(self._h, mu.shape[0], _ptr(mu), _ptr(x), _ptr(y),
                                    C.c_void_p(int(stream) if stream else 0)))
+
+    def products(self, R=None, E=None, engine="auto"):
+        """rb_products: (W^T R, W E) for FP32 batches R [B][N_dof] and E [B][n] (host arrays)."""
+        R = None if R is None else np.ascontiguousarray(R, dtype=np.float32)
+        E = None if E is None else np.ascontiguousarray(E, dtype=np.float32)
+        B = (R if R is not None else E).shape[0]
+        WtR = None if R is None else np.zeros((B, self.n))
+        WE = None if E is None else np.zeros((B, self.n_dof), dtype=np.float32)
+        eng = GEMMS[engine] if isinstance(engine, str) else engine
+        self._check(lib().rb_products(self._h, B, _ptr(R), _ptr(WtR), _ptr(E), _ptr(WE), eng))
+        return WtR, WE
 
     def profile(self, enable: bool) -> None:
         """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""

@@ -208,6 +208,34 @@ def test_rowmarch_2d_matches_oracle(dims):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,n", [((128, 96), 8), ((256, 33), 40), ((64, 64), 100)])
+def test_batched_products_both_engines(dims, n):
+    """W^T R (eq. 5) and W E (eq. 7) against FP64 numpy: FP32 CUDA cores to 1e-5, TF32 tensor cores to
+    the TF32 rounding level (10-bit mantissa: 2e-3 relative in the Frobenius norm)."""
+    w = wl.small(dims, (2, 2), n_basis=1)
+    prob = w.problem
+    rng = np.random.default_rng(5)
+    W, _ = np.linalg.qr(rng.standard_normal((prob.n_dof, n)))
+    ANq = np.stack([np.eye(n)] * prob.P)
+    fNr = np.zeros((1, n))
+    B = 130                                  # two query tiles of 128, the second ragged
+    ctx = rb.Context.from_arrays(prob, W, ANq, fNr, max_batch=B)
+    R = rng.standard_normal((B, prob.n_dof)).astype(np.float32)
+    E = rng.standard_normal((B, n)).astype(np.float32)
+    ref_p = R.astype(np.float64) @ W
+    ref_y = E.astype(np.float64) @ W.T
+    fro = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    p_c, y_c = ctx.products(R, E, engine="cuda_cores")
+    assert fro(p_c, ref_p) < 1e-5 and fro(y_c, ref_y) < 1e-5
+    p_t, y_t = ctx.products(R, E, engine="tensor")
+    assert fro(p_t, ref_p) < 2e-3 and fro(y_t, ref_y) < 2e-3
+    # row by row (every query of both tiles) and column by column
+    assert np.max(np.linalg.norm(p_t - ref_p, axis=1) / np.linalg.norm(ref_p, axis=1)) < 5e-3
+    assert np.max(np.linalg.norm(y_t - ref_y, axis=1) / np.linalg.norm(ref_y, axis=1)) < 5e-3
+    assert np.max(np.linalg.norm(p_t - ref_p, axis=0) / np.linalg.norm(ref_p, axis=0)) < 5e-3
+    ctx.close()
+
+
 def test_3d_fp64_and_mixed():
     w = wl.small((14, 12, 10), (2, 2, 2), n_basis=6, n_train=24)
     prob = w.problem
