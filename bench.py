@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--fp64-queries", type=int, default=256, help="queries of the FP64 plain comparator (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40, help="Alg. 3 iterations per core in the CPU sample")
+    ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no per-kernel pass, e2e, FP64 comparator or CPU baseline); for profilers")
     return ap.parse_args()
 
 
@@ -189,7 +192,12 @@ def main():
 
     # ---- offline (not timed): greedy basis on the GPU
     t0 = time.perf_counter()
-    ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B)
+    if args.basis and os.path.exists(args.basis):
+        ctx = rb.Context.load(args.basis, max_batch=B)
+    else:
+        ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B)
+        if args.basis:
+            ctx.save(args.basis)
     offline_s = time.perf_counter() - t0
     _, _, _, _, sel = ctx.basis()
 
@@ -231,6 +239,17 @@ def main():
     value = world * B * args.steps / t_max
     last = stats[-1]
     ok = bool(np.all(last["status"] == rb.RB_OK))
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
+                              "quick": True, "all_converged": ok, "mean_iters": float(last["iters"].mean()),
+                              "config": {"workload": w.name, "queries_per_step_per_gpu": B}}))
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # ---- per-kernel device time (CUDA events around every launch; separate pass)
     ctx.profile(True)
