@@ -77,7 +77,7 @@ struct Params {
     int nb, nbp;                 // basis size and padded stride
     const double* W64c;
     const float* W32c;
-    const double* L;             // [Bmax][nbp][nbp] Cholesky factors (lower, row-major)
+    const double* L;             // [Bmax][nbp][nbp] A_N(mu)^{-1} (row-major, formed from the Cholesky factor)
     // vectors
     double* x64;                 // [B][N] FP64 iterate / solution
     void* r;                     // [B][N] of T (updated in place)

@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(THREADS) k_project(Params P) {
     }
 }
 
-// e_N = A_N(mu)^{-1} r_N by forward / backward substitution with L (one warp per query)
+// e_N = A_N(mu)^{-1} r_N (eq. 6).  r_N is the fixed-order sum of the projection
+// partials; A_N^{-1} was formed from the Cholesky factor when the query started
+// (k_cholesky), so each iteration is one dense matvec (one warp per query,
+// coalesced rows of the symmetric inverse).
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_reduced_solve(Params P) {
     __shared__ double buf[THREADS / 32][MAX_N];
@@ -95,25 +98,25 @@ __global__ void __launch_bounds__(THREADS) k_reduced_solve(Params P) {
             v[k] = s;
         }
         __syncwarp();
-        const double* L = P.L + (size_t)q * nbp * nbp;
-        // L z = r_N
-        for (int i = 0; i < nb; ++i) {
-            const double zi = v[i] / L[(size_t)i * nbp + i];
-            __syncwarp();
-            if (lane == 0) v[i] = zi;
-            for (int k = i + 1 + lane; k < nb; k += 32) v[k] -= L[(size_t)k * nbp + i] * zi;
-            __syncwarp();
-        }
-        // L^T e = z
-        for (int i = nb - 1; i >= 0; --i) {
-            const double ei = v[i] / L[(size_t)i * nbp + i];
-            __syncwarp();
-            if (lane == 0) v[i] = ei;
-            for (int k = lane; k < i; k += 32) v[k] -= L[(size_t)i * nbp + k] * ei;
-            __syncwarp();
+        const double* Ai = P.L + (size_t)q * nbp * nbp;
+        double acc[MAX_N / 32];
+#pragma unroll
+        for (int t = 0; t < MAX_N / 32; ++t) acc[t] = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            const double vj = v[j];
+            const double* row = Ai + (size_t)j * nbp;
+#pragma unroll
+            for (int t = 0; t < MAX_N / 32; ++t) {
+                const int k = lane + 32 * t;
+                if (k < nb) acc[t] += row[k] * vj;
+            }
         }
         T* e = reinterpret_cast<T*>(P.e) + (size_t)q * P.lde;
-        for (int k = lane; k < P.lde; k += 32) e[k] = k < nb ? (T)v[k] : T(0);
+#pragma unroll
+        for (int t = 0; t < MAX_N / 32; ++t) {
+            const int k = lane + 32 * t;
+            if (k < P.lde) e[k] = k < nb ? (T)acc[t] : T(0);
+        }
         __syncwarp();
     }
 }
@@ -191,8 +194,8 @@ template void launch_prolong<float>(const Params&, const Launch&, bool);
 template void launch_prolong<double>(const Params&, const Launch&, bool);
 
 // ----------------------------------------------------------------------------
-// A_N(mu) = sum_q mu_q A_{N,q} and its Cholesky factor, one CTA per query.
-// ANq is [Q][nb][nb]; L is written [q][nbp][nbp], zero above the diagonal.
+// A_N(mu) = sum_q mu_q A_{N,q}, its Cholesky factor (breakdown on a non-positive
+// pivot) and, from the factor, A_N^{-1} written to [q][nbp][nbp]; one CTA per query.
 
 __global__ void __launch_bounds__(THREADS) k_cholesky(Params P, const double* __restrict__ ANq, int Q) {
     extern __shared__ double A[];
@@ -226,10 +229,22 @@ __global__ void __launch_bounds__(THREADS) k_cholesky(Params P, const double* __
         }
         __syncthreads();
     }
-    double* L = const_cast<double*>(P.L) + (size_t)q * nbp * nbp;
-    for (int idx = threadIdx.x; idx < nbp * nbp; idx += THREADS) {
-        const int i = idx / nbp, k = idx % nbp;
-        L[idx] = (i < nb && k < nb && k <= i) ? A[i * nb + k] : (i == k ? 1.0 : 0.0);
+    // A_N^{-1} = L^{-T} L^{-1}, column j by the two triangular solves L z = e_j,
+    // L^T x = z (thread j owns column j of the output; the output doubles as z)
+    double* Ai = const_cast<double*>(P.L) + (size_t)q * nbp * nbp;
+    if (!bad) {
+        for (int j = threadIdx.x; j < nb; j += THREADS) {
+            for (int i = 0; i < nb; ++i) {
+                double sacc = (i == j) ? 1.0 : 0.0;
+                for (int k = j; k < i; ++k) sacc -= A[i * nb + k] * Ai[(size_t)k * nbp + j];
+                Ai[(size_t)i * nbp + j] = i < j ? 0.0 : sacc / A[i * nb + i];
+            }
+            for (int i = nb - 1; i >= 0; --i) {
+                double sacc = Ai[(size_t)i * nbp + j];
+                for (int k = i + 1; k < nb; ++k) sacc -= A[k * nb + i] * Ai[(size_t)k * nbp + j];
+                Ai[(size_t)i * nbp + j] = sacc / A[i * nb + i];
+            }
+        }
     }
     if (bad && threadIdx.x == 0) {
         QState& s = P.st[q];

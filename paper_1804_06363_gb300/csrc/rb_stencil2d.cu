@@ -50,8 +50,17 @@ template <typename T> __device__ __forceinline__ V4<T> zero4() { return V4<T>{{T
 template <typename T>
 struct RowCoef {
     T kx[5];     // x faces: kx[j] between points j-1 and j (kx[0], kx[4] reach the neighbour threads)
-    T kym[4], kyp[4], diag[4];
+    T kym[4], kyp[4], diag[4], idiag[4];
 };
+
+// The coefficients of row k depend only on the y-blocks of rows k-1, k, k+1 (and on
+// whether those rows exist): rows with equal keys share their coefficients.
+__device__ __forceinline__ int row_key(const Geo& g, int k) {
+    const int c = __ldg(g.by + k);
+    const int m = k > 0 ? __ldg(g.by + k - 1) : 0xFF;
+    const int p = k < g.my - 1 ? __ldg(g.by + k + 1) : 0xFF;
+    return c | (m << 8) | (p << 16);
+}
 
 template <typename T>
 struct ColMap {
@@ -80,6 +89,18 @@ __device__ __forceinline__ void row_coef(const Geo& g, const T* mus, const ColMa
         c.kym[j] = hy * (up ? half * (mc + mus[cm.b[j + 1] + bym]) : mc);
         c.kyp[j] = hy * (dn ? half * (mc + mus[cm.b[j + 1] + byp]) : mc);
         c.diag[j] = c.kx[j] + c.kx[j + 1] + c.kym[j] + c.kyp[j];
+        c.idiag[j] = T(1) / c.diag[j];
+    }
+}
+
+// row_coef with a one-entry cache keyed by row_key (uniform across the CTA)
+template <typename T>
+__device__ __forceinline__ void row_coef_cached(const Geo& g, const T* mus, const ColMap<T>& cm, int k, int& ckey,
+                                                RowCoef<T>& c) {
+    const int key = row_key(g, k);
+    if (key != ckey) {
+        row_coef(g, mus, cm, k, c);
+        ckey = key;
     }
 }
 
@@ -214,6 +235,8 @@ __global__ void __launch_bounds__(256) k2_cg_a(Params P) {
         V4<T> vm = prow(y0 - 1), vc = prow(y0);
         T acc = T(0);
         int buf = 0;
+        RowCoef<T> c;
+        int ckey = -1;
         for (int k = y0; k < y1; ++k) {
             const V4<T> vp = prow(k + 1);
             T left, right;
@@ -221,8 +244,7 @@ __global__ void __launch_bounds__(256) k2_cg_a(Params P) {
             buf ^= 1;
             if (!cm.left) left = T(0);
             if (!cm.right) right = T(0);
-            RowCoef<T> c;
-            row_coef(g, mus, cm, k, c);
+            row_coef_cached(g, mus, cm, k, ckey, c);
             const V4<T> av = apply_row(c, vm, vc, vp, left, right);
             st4(pn + (size_t)k * mx, vc);
 #pragma unroll
@@ -279,6 +301,8 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
         V4<T> vm = prow(y0 - 1), vc = prow(y0);
         T acc = T(0);
         int buf = 0;
+        RowCoef<T> c;
+        int ckey = -1;
         for (int k = y0; k < y1; ++k) {
             const V4<T> vp = prow(k + 1);
             const V4<T> dk = ld4(d + (size_t)k * mx);
@@ -288,8 +312,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
             buf ^= 1;
             if (!cm.left) left = T(0);
             if (!cm.right) right = T(0);
-            RowCoef<T> c;
-            row_coef(g, mus, cm, k, c);
+            row_coef_cached(g, mus, cm, k, ckey, c);
             const V4<T> av = apply_row(c, vm, vc, vp, left, right);
             V4<T> dn, rnew;
 #pragma unroll
@@ -365,7 +388,8 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
         V4<T> zm = zero4<T>(), zc = zero4<T>();
         V4<T> rc = zero4<T>();
         V4<T> pm = zero4<T>(), pc = zero4<T>();
-        RowCoef<T> cprev;
+        RowCoef<T> cprev, ccache;
+        int ckey = -1;
         T ry = T(0), apy = T(0);
         int buf = 0;
         for (int k = y0 - 1; k <= y1; ++k) {
@@ -395,9 +419,9 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
             buf ^= 1;
             // red half-sweep on row k (inside the grid)
             V4<T> zk = zero4<T>();
-            RowCoef<T> ck;
             if (k >= 0 && k < my) {
-                row_coef(g, mus, cm, k, ck);
+                row_coef_cached(g, mus, cm, k, ckey, ccache);
+                const RowCoef<T>& ck = ccache;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (((j + k) & 1) == 0) {
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
                         const T xr = j == 3 ? rgt[0] : sc.v[j + 1];
                         const T num = rk.v[j] + ck.kx[j] * xl + ck.kx[j + 1] * xr + ck.kym[j] * sm.v[j] +
                                       ck.kyp[j] * sp.v[j];
-                        zk.v[j] = num / ck.diag[j];
+                        zk.v[j] = num * ck.idiag[j];
                     }
                 }
             }
@@ -422,7 +446,7 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
                         const T xr = j == 3 ? rgt[1] : zc.v[j + 1];
                         const T num = rc.v[j] + cprev.kx[j] * xl + cprev.kx[j + 1] * xr + cprev.kym[j] * zm.v[j] +
                                       cprev.kyp[j] * zk.v[j];
-                        out.v[j] = num / cprev.diag[j];
+                        out.v[j] = num * cprev.idiag[j];
                     }
                 }
                 st4(dst + (size_t)kb * mx, out);
@@ -443,7 +467,7 @@ __global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__
             rc = rk;
             pm = pc;
             pc = pk;
-            cprev = ck;
+            cprev = ccache;
         }
         if (LAST) {
             double v[2];

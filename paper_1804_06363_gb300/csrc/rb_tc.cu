@@ -5,10 +5,11 @@
 //                 split-K over the points (partials reduced in FP64 by the
 //                 reduced-solve kernel, fixed order), one CTA per (query tile,
 //                 split);
-//   prolongation  Y (128 queries x 128 points) = E (128 x n) * W32r^T,
+//   prolongation  Y^T (128 points x 128 queries) = W32r tile (128 x n) * E^T,
 //                 one CTA per (query tile, range of point tiles), accumulators
 //                 double-buffered in TMEM so the epilogue of one tile overlaps
-//                 the MMAs of the next.
+//                 the MMAs of the next; the point is the TMEM lane, so stores of
+//                 one query by a warp are contiguous.
 // Operands are staged by TMA (128-byte swizzle) and consumed by
 // tcgen05.mma.kind::tf32 issued by one thread; accumulators live in TMEM and
 // are read back with tcgen05.ld by four epilogue warps.  Warp 0 is the TMA
@@ -254,19 +255,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // ---------------------------------------------------------------------------
 // prolongation: ypro[q][i] = sum_k e[q][k] W[i][k]
+// D (128 points x 128 queries) = W32r tile (points x K) * E tile (queries x K)^T:
+// the TMEM lane is the point, so a warp's store for one query covers 32
+// consecutive points (128 contiguous bytes).
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_prolong(const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_wr, Params P,
                  int ctas_per_m, int stages, int ksub, int* err) {
     extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_act[128];
     unsigned char* sm = align1024(smem_raw);
     constexpr uint32_t SUB = 128 * 128;   // one 128-row x 32-float swizzled sub-tile
-    unsigned char* sA = sm;                                         // ksub sub-tiles
-    unsigned char* sB = sm + (size_t)ksub * SUB;                    // stages x ksub sub-tiles
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)stages * ksub * SUB);
+    unsigned char* sE = sm;                                         // ksub sub-tiles (queries)
+    unsigned char* sW = sm + (size_t)ksub * SUB;                    // stages x ksub sub-tiles (points)
+    uint64_t* full = reinterpret_cast<uint64_t*>(sW + (size_t)stages * ksub * SUB);
     uint64_t* empty = full + stages;
-    uint64_t* afull = empty + stages;
-    uint64_t* tfull = afull + 1;     // [2]
+    uint64_t* efull = empty + stages;
+    uint64_t* tfull = efull + 1;     // [2]
     uint64_t* tempty = tfull + 2;    // [2]
     uint64_t* done = tempty + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
@@ -275,7 +280,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mtile = blockIdx.x / ctas_per_m, c = blockIdx.x % ctas_per_m;
     const int q0 = mtile * 128;
-    if (!tile_active(P, q0)) return;
+    if (threadIdx.x < 128) {
+        const int q = q0 + threadIdx.x;
+        s_act[threadIdx.x] = (q < P.B && P.st[q].phase == PH_PREC) ? 1 : 0;
+    }
+    if (!__syncthreads_or(threadIdx.x < 128 ? s_act[threadIdx.x] : 0)) return;
     const long long n = P.g.n;
     const int nptiles = (int)((n + 127) / 128);
     const int per = (nptiles + ctas_per_m - 1) / ctas_per_m;
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
-        mbar_init(afull, 1);
+        mbar_init(efull, 1);
         mbar_init(tfull + 0, 1);
         mbar_init(tfull + 1, 1);
         mbar_init(tempty + 0, 4);
@@ -307,21 +316,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0 && np > 0) {
             int last_use[8];
             for (int s = 0; s < 8; ++s) last_use[s] = -1;
-            bool a_issued = false;
-            mbar_expect_tx(afull, (uint32_t)ksub * SUB);
-            for (int k = 0; k < ksub; ++k) tma2d(sA + (size_t)k * SUB, &tm_e, afull, 32 * k, q0);
-            a_issued = true;
+            mbar_expect_tx(efull, (uint32_t)ksub * SUB);
+            for (int k = 0; k < ksub; ++k) tma2d(sE + (size_t)k * SUB, &tm_e, efull, 32 * k, q0);
             for (int i = 0; i < np; ++i) {
                 const int s = i % stages;
                 const int use = i / stages;
                 if (use > 0 && !mbar_wait(empty + s, (use - 1) & 1, err)) break;
                 mbar_expect_tx(full + s, (uint32_t)ksub * SUB);
                 for (int k = 0; k < ksub; ++k)
-                    tma2d(sB + ((size_t)s * ksub + k) * SUB, &tm_wr, full + s, 32 * k, (p0 + i) * 128);
+                    tma2d(sW + ((size_t)s * ksub + k) * SUB, &tm_wr, full + s, 32 * k, (p0 + i) * 128);
                 last_use[s] = use;
             }
             if (*(volatile int*)err) {
-                if (a_issued) mbar_drain(afull, 0);
+                mbar_drain(efull, 0);
                 for (int s = 0; s < stages && s < 8; ++s)
                     if (last_use[s] >= 0) mbar_drain(full + s, last_use[s] & 1);
             }
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, 128);
-            bool ok = np > 0 ? mbar_wait(afull, 0, err) : false;
+            bool ok = np > 0 ? mbar_wait(efull, 0, err) : false;
             for (int i = 0; ok && i < np; ++i) {
                 const int s = i % stages;
                 const int use = i / stages;
@@ -338,8 +345,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (i >= 2 && !mbar_wait(tempty + ab, ((i >> 1) - 1) & 1, err)) break;
                 tc_fence_after();
                 for (int k = 0; k < ksub; ++k) {
-                    const uint64_t ad = sdesc_sw128(s2u(sA + (size_t)k * SUB));
-                    const uint64_t bd = sdesc_sw128(s2u(sB + ((size_t)s * ksub + k) * SUB));
+                    const uint64_t ad = sdesc_sw128(s2u(sW + ((size_t)s * ksub + k) * SUB));
+                    const uint64_t bd = sdesc_sw128(s2u(sE + (size_t)k * SUB));
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         umma_tf32(tmem + (uint32_t)(ab * 128), ad + 2 * j, bd + 2 * j, idesc,
@@ -353,24 +360,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else {
         const int quad = warp & 3;
-        const int q = q0 + quad * 32 + lane;
-        const bool write = q < P.B && P.st[q].phase == PH_PREC;
-        float* yq = reinterpret_cast<float*>(P.ypro) + (size_t)q * n;
+        const int prow = quad * 32 + lane;          // point within the tile (TMEM lane)
+        float* ybase = reinterpret_cast<float*>(P.ypro) + (size_t)q0 * n;
         for (int i = 0; i < np; ++i) {
             const int ab = i & 1;
             bool ok = mbar_wait(tfull + ab, (i >> 1) & 1, err);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc_fence_after();
-            const long long pt0 = (long long)(p0 + i) * 128;
+            const long long pt = (long long)(p0 + i) * 128 + prow;
+            const bool inside = pt < n;
             for (int cc = 0; cc < 128; cc += 16) {
                 float v[16];
                 tmem_ld16(tmem + (uint32_t)(ab * 128) + ((uint32_t)(quad * 32) << 16) + (uint32_t)cc, v);
-                if (write && pt0 + cc < n) {
-                    float4* dst = reinterpret_cast<float4*>(yq + pt0 + cc);
+                if (inside) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        __stcs(dst + t, make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]));
+                    for (int j = 0; j < 16; ++j)
+                        if (s_act[cc + j]) __stcs(ybase + (size_t)(cc + j) * n + pt, v[j]);
                 }
             }
             tc_fence_before();
@@ -378,7 +384,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) mbar_arrive(tempty + ab);
         }
         if (np > 0) {
-            // all MMAs finished before TMEM is released
             if (lane == 0) mbar_drain(done, 0);
             __syncwarp();
         }
