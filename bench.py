@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40, help="Alg. 3 iterations per core in the CPU sample")
     ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --nu, --gemm as given)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no per-kernel pass, e2e, FP64 comparator or CPU baseline); for profilers")
     return ap.parse_args()
@@ -208,6 +209,14 @@ def main():
     stream = torch.cuda.current_stream(dev)
     opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, stream=stream.cuda_stream)
 
+    # ---- autotuner (setup, not timed): on training parameters, never on the timed test queries
+    tuned = None
+    if not args.no_tune:
+        tB = min(B, 256)
+        tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
+        opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"])
+        tuned["sample"] = f"{tB} training parameters"
+
     def step(xbuf, **kw):
         status, st = ctx.pcg(mu, xbuf, **{**opts, **kw})
         return status, st
@@ -261,15 +270,18 @@ def main():
     prec = "f32" if args.precision == "mixed" else "f64"
     iters = int(st_prof["iters"].sum())
     outers = int(st_prof["outer"].sum())
-    units = {"cg_a": iters, "cg_b": iters, "smooth": iters * max(1, args.nu), "project": iters,
+    units = {"cg_a": iters, "cg_b": iters, "smooth": iters * max(1, opts["nu"]), "project": iters,
              "tc_project": iters, "prolong": iters, "tc_prolong": iters, "outer_residual": outers,
              "outer_update": outers}
     kernels = {}
+    es = 4 if prec == "f32" else 8
     for k, (n_launch, ms) in prof.items():
         bpp = BYTES_PER_POINT[prec].get(k)
         entry = {"launches": n_launch, "ms": round(ms, 3)}
         if bpp is not None and ms > 0:
             alg = bpp * N * units[k]
+            if k == "smooth":   # nu sweeps: the last one also reads the direction p (PR term)
+                alg = (bpp + 3 * es * (max(1, opts["nu"]) - 1)) * N * iters
             entry["alg_bytes"] = alg
             entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
         kernels[k] = entry
@@ -303,15 +315,21 @@ def main():
     if args.fp64_queries > 0 and args.precision == "mixed":
         q64 = min(B, args.fp64_queries)
         x64 = torch.zeros((q64, N), dtype=torch.float64, device=dev)
-        ctx.pcg(mu[:q64], x64, **{**opts, "precision": "fp64"})
+        opts64 = {**opts, "precision": "fp64"}
+        tuned64 = None
+        if not args.no_tune:
+            tuned64 = ctx.autotune(w.train_mu()[:64], x64[:64], **opts64)
+            opts64.update(nu=tuned64["nu"])
+        ctx.pcg(mu[:q64], x64, **opts64)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, st64 = ctx.pcg(mu[:q64], x64, **{**opts, "precision": "fp64"})
+        _, st64 = ctx.pcg(mu[:q64], x64, **opts64)
         b.record(stream)
         torch.cuda.synchronize()
         s64 = a.elapsed_time(b) / 1000.0
-        fp64 = {"value": q64 / s64, "unit": "solves/s", "queries": q64,
+        fp64 = {"value": q64 / s64, "unit": "solves/s", "queries": q64, "nu": opts64["nu"],
+                "tuned": tuned64,
                 "mean_iters": float(st64["iters"].mean()), "all_converged": bool(np.all(st64["status"] == 0)),
                 "max_rel_res": float(st64["rel_res"].max())}
 
@@ -341,7 +359,8 @@ def main():
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": w.name, "grid": "x".join(map(str, prob.dims)), "P": prob.P, "n_basis": w.n_basis,
                        "queries_per_step_per_gpu": B, "precision": args.precision, "beta": "pr",
-                       "smoother": f"red-black GS nu={args.nu}", "tol": 1e-10, "gemm": args.gemm,
+                       "smoother": f"red-black GS nu={opts['nu']}", "tol": 1e-10, "gemm": opts["gemm"],
+                       "inner_tol": opts.get("inner_tol"), "autotuned": tuned,
                        "l2": "inputs larger than L2 (FP64 solutions %.1f GB + FP32 work vectors per step)"
                              % (B * N * 8 / 1e9),
                        "offline_build_s": round(offline_s, 1), "greedy_selected_first": [int(s) for s in sel[:8]]},

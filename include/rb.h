@@ -177,6 +177,22 @@ rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const flo
 rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y,
                    void* stream);
 
+/* Autotuner.  Times rb_pcg on the B sample queries (host mu; x host or device
+ * [B][N_dof] scratch) and picks, by coordinate descent from *opts, the smoother
+ * sweep count nu (1..6; the paper leaves the smoother's iteration count open,
+ * Section 3.1), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6; mixed only)
+ * and the GEMM engine (mixed only).  Only configurations under which every
+ * sample query converges are eligible.  Writes the fastest into *opts and
+ * summarises it in *res (may be NULL). */
+typedef struct {
+    int nu;
+    double inner_tol;
+    int gemm;
+    double ms_per_solve;   /* of the chosen configuration on the sample */
+    int trials;
+} rb_tune_result;
+rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* opts, rb_tune_result* res);
+
 /* Per-kernel timing.  rb_profile(ctx, 1) clears the counters and from then on
  * brackets every kernel launch of rb_solve / rb_pcg with CUDA events on the
  * call's stream (the iteration body is then launched directly, not as a CUDA

@@ -10,7 +10,8 @@ Readings of the paper (where it is silent or loose):
     (the relative residual of eq. relerr); it is applied to the recurrence
     residual, and at exit the true residual f - A x is recomputed: if it is
     not below tol either, the residual is replaced by the true one and the
-    iteration restarts from the current x (counted in the same budget);
+    iteration restarts from the current x (counted in the same budget),
+    aiming at tol/2 so that the next true residual clears tol;
   * Alg. 3 step 1 writes A without mu; it is A(mu).  With x_0 = 0 the first
     residual is f itself, so no matrix-vector product is spent on it;
   * RBI(A, r, W, 1) inside Alg. 3 starts from x = 0, so its own residual is r:
@@ -167,8 +168,9 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
         r = b - A(x)
     hist = [np.linalg.norm(r) / bn]
     it, restarts = 0, 0
+    target = tol
     while True:
-        y = Minv(r) if hist[-1] >= tol else None
+        y = Minv(r) if hist[-1] >= target else None
         p = None if y is None else y.copy()
         rho = None if y is None else r @ y
         while y is not None and it < max_iter:
@@ -179,7 +181,7 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
             r = r - alpha * q
             it += 1
             hist.append(np.linalg.norm(r) / bn)
-            if hist[-1] < tol:
+            if hist[-1] < target:
                 break
             y = Minv(r)
             rho_new = r @ y
@@ -199,3 +201,4 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
         r = r_true
         hist[-1] = rel
         restarts += 1
+        target = 0.5 * tol

@@ -834,6 +834,70 @@ rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const flo
     return RB_OK;
 }
 
+rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* opts, rb_tune_result* res) {
+    if (!ctx || !opts || B < 1 || !mu || !x) {
+        if (ctx) ctx->err = "rb_autotune needs opts, B >= 1, mu and x";
+        return RB_EINVAL;
+    }
+    TRY(validate_opts(ctx, *opts));
+    cudaStream_t s = opts->stream ? (cudaStream_t)opts->stream : ctx->own_stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<rb_stats> st(B);
+    int trials = 0;
+    // time of one batch (after one untimed run); +inf if a query does not converge
+    auto trial = [&](const rb_opts& t) -> double {
+        ++trials;
+        if (rb_pcg(ctx, B, mu, x, &t, st.data()) != RB_OK) return 1e300;
+        cudaEventRecord(e0, s);
+        const rb_status r = rb_pcg(ctx, B, mu, x, &t, st.data());
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return r == RB_OK ? (double)ms : 1e300;
+    };
+    rb_opts best = *opts;
+    double best_ms = trial(best);
+    for (int nu = 1; nu <= 6; ++nu) {
+        if (nu == best.nu) continue;
+        rb_opts t = best;
+        t.nu = nu;
+        const double ms = trial(t);
+        if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    if (best.precision == RB_PREC_MIXED) {
+        const double tols[3] = {1e-4, 1e-5, 1e-6};
+        const rb_opts base = best;
+        for (double it : tols) {
+            if (it == base.inner_tol) continue;
+            rb_opts t = base;
+            t.inner_tol = it;
+            const double ms = trial(t);
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+        if (tc_usable(ctx->tc, ctx->n)) {
+            rb_opts t = best;
+            t.gemm = best.gemm == RB_GEMM_CUDA_CORES ? RB_GEMM_TENSOR : RB_GEMM_CUDA_CORES;
+            const double ms = trial(t);
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e299) { ctx->err = "no candidate configuration converged on the sample"; return RB_ENOCONV; }
+    *opts = best;
+    if (res) {
+        res->nu = best.nu;
+        res->inner_tol = best.inner_tol;
+        res->gemm = best.gemm;
+        res->ms_per_solve = best_ms / B;
+        res->trials = trials;
+    }
+    return RB_OK;
+}
+
 rb_status rb_solve(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts* opts, rb_stats* stats) {
     return run_batch(ctx, B, mu, x, opts, stats, Mode{true, false});
 }

@@ -84,13 +84,15 @@ __device__ void finalize_outer(const Params& P, int q, double rr, double ff) {
     if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
     if (s.rel_res < P.tol) { mark_done(P, s, RB_OK); return; }
     if (s.iters >= P.max_iter || s.outer > P.max_outer) { mark_done(P, s, RB_ENOCONV); return; }
-    // a full CG cycle that did not halve the true residual has hit the
-    // rounding floor of the FP64 residual: stop instead of cycling
-    if (s.outer > 2 && s.rel_res > 0.5 * prev) { mark_done(P, s, RB_ENOCONV); return; }
+    // a full CG cycle that gained less than 10% on the true residual has hit
+    // the rounding floor of the FP64 residual: stop instead of cycling
+    if (s.outer > 2 && s.rel_res > 0.9 * prev) { mark_done(P, s, RB_ENOCONV); return; }
     if (s.outer > 1 && !P.mixed) s.restarts += 1;
     // mixed: each FP32 cycle reduces its own residual by inner_tol, but never
     // aims below half the outer tolerance (the FP64 step then finishes).
-    s.target = P.mixed ? fmax(P.inner_tol * rn, 0.5 * P.tol * fn) : P.tol * fn;
+    // FP64: the first cycle stops at tol (Alg. 3 step 8); a restart after a
+    // failed true-residual check aims at half of it.
+    s.target = P.mixed ? fmax(P.inner_tol * rn, 0.5 * P.tol * fn) : (s.outer > 1 ? 0.5 : 1.0) * P.tol * fn;
     s.phase = PH_PREC;
     s.start = 1;
     list_push(P, L_PREC, q);

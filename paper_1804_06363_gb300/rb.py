@@ -50,6 +50,11 @@ class RbBuildOpts(C.Structure):
                 ("drop_tol", C.c_double)]
 
 
+class RbTuneResult(C.Structure):
+    _fields_ = [("nu", C.c_int), ("inner_tol", C.c_double), ("gemm", C.c_int), ("ms_per_solve", C.c_double),
+                ("trials", C.c_int)]
+
+
 class RbKernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_longlong), ("ms", C.c_double)]
 
@@ -73,6 +78,8 @@ SIGNATURES = {
     "rb_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
     "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_products": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rb_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts),
+                              C.POINTER(RbTuneResult)]),
     "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
     "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -292,6 +299,16 @@ class Context:
         eng = GEMMS[engine] if isinstance(engine, str) else engine
         self._check(lib().rb_products(self._h, B, _ptr(R), _ptr(WtR), _ptr(E), _ptr(WE), eng))
         return WtR, WE
+
+    def autotune(self, mu, x, **kw) -> dict:
+        """rb_autotune: fastest (nu, inner_tol, gemm) on the sample queries; returns the chosen options."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        o = make_opts(**kw)
+        r = RbTuneResult()
+        self._check(lib().rb_autotune(self._h, mu.shape[0], _ptr(mu), _ptr(x), C.byref(o), C.byref(r)))
+        inv = {v: k for k, v in GEMMS.items()}
+        return {"nu": r.nu, "inner_tol": r.inner_tol, "gemm": inv.get(r.gemm, r.gemm),
+                "ms_per_solve": r.ms_per_solve, "trials": r.trials}
 
     def profile(self, enable: bool) -> None:
         """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""
