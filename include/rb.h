@@ -83,6 +83,8 @@ typedef struct {
     int max_outer;      /* mixed: maximum FP64 refinement steps */
     int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
     int graph;          /* 1: replay the iteration body as a captured CUDA graph */
+    int kernels;        /* 0: one pass over memory per smoother sweep;
+                           1: all sweeps fused in one pass (FP32 mixed path, 2D, nu <= 6) */
     void* stream;       /* cudaStream_t or NULL */
 } rb_opts;
 
@@ -172,6 +174,15 @@ rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x,
  * context's workspace (overwrites solver state; not during a solve). */
 rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const float* E, float* WE, int engine);
 
+/* The RB preconditioner of Alg. 3 (steps 2 and 9): y_b = RBI(A(mu_b), r_b, W, 1)
+ * from zero, i.e. y = W A_N^{-1} W^T r (eqs. 5-7) followed by opts->nu sweeps of
+ * the smoother S(A, r, y) (eq. 8).  opts->precision selects FP64 (r, y double)
+ * or the mixed inner precision (r, y float; TF32 or FP32 products, FP32
+ * smoother); opts->kernels and opts->gemm select the kernels.  mu host
+ * [B][n_mu]; r, y host or device [B][N_dof]; B <= max_batch.  Uses the
+ * context's workspace (not during a solve).  RB_EBREAKDOWN if A_N(mu) is not SPD. */
+rb_status rb_precondition(rb_ctx* ctx, int B, const double* mu, const void* r, void* y, const rb_opts* opts);
+
 /* y = A(mu_b) x_b for every query b (eq. 1 operator, FP64).  x, y host or device
  * [B][N_dof]; stream as in rb_opts (may be NULL). */
 rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y,
@@ -180,8 +191,8 @@ rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double
 /* Autotuner.  Times rb_pcg on the B sample queries (host mu; x host or device
  * [B][N_dof] scratch) and picks, by coordinate descent from *opts, the smoother
  * sweep count nu (1..6; the paper leaves the smoother's iteration count open,
- * Section 3.1), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6; mixed only)
- * and the GEMM engine (mixed only).  Only configurations under which every
+ * Section 3.1), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6; mixed only),
+ * the smoother kernels (rb_opts.kernels) and the GEMM engine (mixed only).  Only configurations under which every
  * sample query converges are eligible.  Writes the fastest into *opts and
  * summarises it in *res (may be NULL). */
 typedef struct {

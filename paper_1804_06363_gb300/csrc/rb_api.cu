@@ -456,6 +456,8 @@ void flush_profile(rb_ctx* ctx) {
     ctx->ev_used = 0;
 }
 
+void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc);
+
 // One step of the per-query state machine for every active query.
 void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
     cudaStream_t s = L.s;
@@ -477,29 +479,7 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
         timed(ctx, KK_OUTER_RES, s, [&] { launch_outer_residual<double>(P, L); });
     }
     cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
-    if (m.mixed) {
-        if (use_tc) {
-            timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
-            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
-            timed(ctx, KK_TC_PROLONG, s, [&] { tc_prolong(ctx->tc, P, L); });
-        } else {
-            timed(ctx, KK_PROJECT, s, [&] { launch_project<float>(P, L); });
-            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
-            timed(ctx, KK_PROLONG, s, [&] { launch_prolong<float>(P, L, false); });
-        }
-        timed(ctx, KK_SMOOTH, s, [&] {
-            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
-            else launch_smoother<float>(P, L, o.nu, false);
-        });
-    } else {
-        timed(ctx, KK_PROJECT, s, [&] { launch_project<double>(P, L); });
-        timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<double>(P, L); });
-        timed(ctx, KK_PROLONG, s, [&] { launch_prolong<double>(P, L, false); });
-        timed(ctx, KK_SMOOTH, s, [&] {
-            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
-            else launch_smoother<double>(P, L, o.nu, false);
-        });
-    }
+    enqueue_prec(ctx, P, L, o, m, use_tc);
     cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
     if (m.mixed) {
         timed(ctx, KK_CG_A, s, [&] { if (rm) launch2d_cg_a<float>(P, L); else launch_cg_a<float>(P, L); });
@@ -511,9 +491,42 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
     cudaMemsetAsync(ctx->d_lcnt + L_ITER, 0, sizeof(int), s);
 }
 
+// The RBI preconditioner y = RBI(A, r, W, 1) for every query on the PREC list.
+void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
+    cudaStream_t s = L.s;
+    const bool rm = use_rowmarch(ctx->geo) && !ctx->force_generic;
+    if (m.mixed) {
+        if (use_tc) {
+            timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
+            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
+            timed(ctx, KK_TC_PROLONG, s, [&] { tc_prolong(ctx->tc, P, L); });
+        } else {
+            timed(ctx, KK_PROJECT, s, [&] { launch_project<float>(P, L); });
+            timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<float>(P, L); });
+            timed(ctx, KK_PROLONG, s, [&] { launch_prolong<float>(P, L, false); });
+        }
+        timed(ctx, KK_SMOOTH, s, [&] {
+            if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic &&
+                use_fused_smoother(ctx->geo, o.nu))
+                launch2d_smooth_fused(P, L, o.nu);
+            else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
+            else launch_smoother<float>(P, L, o.nu, false);
+        });
+    } else {
+        timed(ctx, KK_PROJECT, s, [&] { launch_project<double>(P, L); });
+        timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<double>(P, L); });
+        timed(ctx, KK_PROLONG, s, [&] { launch_prolong<double>(P, L, false); });
+        timed(ctx, KK_SMOOTH, s, [&] {
+            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
+            else launch_smoother<double>(P, L, o.nu, false);
+        });
+    }
+}
+
 rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
+        (o.kernels != 0 && o.kernels != 1) ||
         (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED)) {
         ctx->err = "invalid options";
         return RB_EINVAL;
@@ -681,6 +694,7 @@ void rb_default_opts(rb_opts* o) {
     o->max_outer = 12;
     o->gemm = RB_GEMM_AUTO;
     o->graph = 1;
+    o->kernels = 0;
     o->stream = nullptr;
 }
 
@@ -834,6 +848,54 @@ rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const flo
     return RB_OK;
 }
 
+rb_status rb_precondition(rb_ctx* ctx, int B, const double* mu, const void* r, void* y, const rb_opts* opts) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || B > ctx->Bmax || (B > 0 && (!mu || !r || !y))) {
+        ctx->err = "need 0 <= B <= max_batch and non-NULL mu, r, y";
+        return RB_EINVAL;
+    }
+    if (B == 0) return RB_OK;
+    rb_opts o;
+    rb_default_opts(&o);
+    if (opts) o = *opts;
+    TRY(validate_opts(ctx, o));
+    for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i)
+        if (!std::isfinite(mu[i])) { ctx->err = "non-finite parameter"; return RB_EINVAL; }
+    const Mode m{false, o.precision == RB_PREC_MIXED};
+    const bool use_tc = m.mixed && o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
+    if (m.mixed && o.gemm == RB_GEMM_TENSOR && !use_tc) { ctx->err = "tensor-core engine unavailable"; return RB_EINVAL; }
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const size_t es = m.mixed ? sizeof(float) : sizeof(double);
+    CK(cudaMemcpyAsync(ctx->d_mu, mu, (size_t)B * ctx->n_mu * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int q = 0; q < B; ++q) {
+        std::memset(&ctx->h_st[q], 0, sizeof(QState));
+        ctx->h_st[q].phase = PH_PREC;
+        ctx->h_st[q].start = 1;
+    }
+    CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
+    std::vector<int> lc(N_LISTS, 0), li(B);
+    lc[L_PREC] = B;
+    for (int q = 0; q < B; ++q) li[q] = q;
+    CK(cudaMemcpyAsync(ctx->d_lcnt, lc.data(), N_LISTS * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lidx + L_PREC * ctx->Bmax, li.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_tick, 0, (size_t)B * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(ctx->d_ndone, 0, sizeof(int), s));
+    Params P = make_params(ctx, B, ctx->d_x64, o, m, use_tc);
+    Launch L{ctx->grid, s};
+    launch_cholesky(P, s, ctx->d_ANq, ctx->P);
+    CK(cudaMemcpyAsync(P.r, r, (size_t)B * N * es, cudaMemcpyDefault, s));
+    if (ctx->n == 0) CK(cudaMemsetAsync(P.ypro, 0, (size_t)B * N * es, s));
+    enqueue_prec(ctx, P, L, o, m, use_tc);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(y, P.y, (size_t)B * N * es, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, (size_t)B * sizeof(QState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < B; ++q)
+        if (ctx->h_st[q].status == RB_EBREAKDOWN) return RB_EBREAKDOWN;
+    return RB_OK;
+}
+
 rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* opts, rb_tune_result* res) {
     if (!ctx || !opts || B < 1 || !mu || !x) {
         if (ctx) ctx->err = "rb_autotune needs opts, B >= 1, mu and x";
@@ -880,6 +942,12 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
         if (tc_usable(ctx->tc, ctx->n)) {
             rb_opts t = best;
             t.gemm = best.gemm == RB_GEMM_CUDA_CORES ? RB_GEMM_TENSOR : RB_GEMM_CUDA_CORES;
+            const double ms = trial(t);
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+        if (best.smoother == RB_SMOOTH_RBGS && use_fused_smoother(ctx->geo, best.nu)) {
+            rb_opts t = best;
+            t.kernels = 1 - best.kernels;
             const double ms = trial(t);
             if (ms < best_ms) { best_ms = ms; best = t; }
         }

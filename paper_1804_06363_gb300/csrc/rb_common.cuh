@@ -194,6 +194,23 @@ __device__ __forceinline__ void mark_done(const Params& P, QState& s, int status
     atomicAdd(P.ndone, 1);
 }
 
+// Preconditioner finalizer: ry = r_{k+1}^T y_{k+1}, apy = (A p_k)^T y_{k+1}.
+// Polak-Ribiere numerator y_{k+1}^T (r_{k+1} - r_k) = -alpha_k apy since
+// r_{k+1} = r_k - alpha_k A p_k; Fletcher-Reeves uses ry (Alg. 3 step 10).
+__device__ __forceinline__ void finalize_prec_state(const Params& P, int q, double ry, double apy) {
+    QState& s = P.st[q];
+    if (!(ry > 0.0)) { mark_done(P, s, RB_EBREAKDOWN); return; }
+    if (s.start) {
+        s.beta = 0.0;
+        s.start = 0;
+    } else {
+        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : -s.alpha * apy / s.rho;
+    }
+    s.rho = ry;
+    s.phase = PH_ITER;
+    list_push(P, L_ITER, q);
+}
+
 // Thread 0 publishes a CTA's partial sums for (q, tile); returns true in every
 // thread of the CTA that is the last to do so for q.  The caller then reduces
 // the partials in a fixed order (deterministic) and resets tick[q].
@@ -243,6 +260,10 @@ bool use_rowmarch(const Geo& g);
 template <typename T> void launch2d_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch2d_cg_b(const Params& P, const Launch& L);
 template <typename T> void launch2d_smooth(const Params& P, const Launch& L, int nu);
+// all nu sweeps in one pass (FP32, dim 2, mx even, nu <= 6)
+bool use_fused_smoother(const Geo& g, int nu);
+void launch2d_smooth_fused(const Params& P, const Launch& L, int nu);
+int fused_tiles(const Geo& g, int nu);
 template <typename T> void launch_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch_cg_b(const Params& P, const Launch& L);
 void launch_rbi_residual(const Params& P, const Launch& L);

@@ -37,7 +37,7 @@ class RbOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("smoother", C.c_int), ("nu", C.c_int),
                 ("omega", C.c_double), ("precision", C.c_int), ("beta_form", C.c_int), ("x0_mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("gemm", C.c_int), ("graph", C.c_int),
-                ("stream", C.c_void_p)]
+                ("kernels", C.c_int), ("stream", C.c_void_p)]
 
 
 class RbStats(C.Structure):
@@ -78,6 +78,7 @@ SIGNATURES = {
     "rb_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
     "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_products": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "rb_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(RbOpts)]),
     "rb_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts),
                               C.POINTER(RbTuneResult)]),
     "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -299,6 +300,17 @@ class Context:
         eng = GEMMS[engine] if isinstance(engine, str) else engine
         self._check(lib().rb_products(self._h, B, _ptr(R), _ptr(WtR), _ptr(E), _ptr(WE), eng))
         return WtR, WE
+
+    def precondition(self, mu, r, **kw) -> np.ndarray:
+        """rb_precondition: y = RBI(A(mu), r, W, 1) for host arrays r [B][N_dof]
+        (float64, or float32 with precision="mixed")."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        mixed = kw.get("precision", "fp64") == "mixed"
+        r = np.ascontiguousarray(r, dtype=np.float32 if mixed else np.float64)
+        y = np.zeros_like(r)
+        o = make_opts(**kw)
+        self._check(lib().rb_precondition(self._h, mu.shape[0], _ptr(mu), _ptr(r), _ptr(y), C.byref(o)))
+        return y
 
     def autotune(self, mu, x, **kw) -> dict:
         """rb_autotune: fastest (nu, inner_tol, gemm) on the sample queries; returns the chosen options."""

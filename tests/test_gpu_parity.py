@@ -208,6 +208,57 @@ def test_rowmarch_2d_matches_oracle(dims):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,blocks", [((128, 100), (3, 3)), ((62, 70), (2, 3)), ((256, 33), (3, 2))])
+@pytest.mark.parametrize("nu", [1, 3, 6])
+def test_fused_smoother_matches_one_sweep_kernels(dims, blocks, nu):
+    """All nu sweeps in one pass (trapezoid strips) give the same preconditioner as nu
+    separate sweeps: same mixed-precision iteration counts (+-2) and the truth solution."""
+    w = wl.small(dims, blocks, n_basis=6, n_train=24, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    res = {}
+    for kernels in (0, 1):
+        x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+        status, st = ctx.pcg(mu, x, precision="mixed", nu=nu, kernels=kernels, gemm="cuda_cores")
+        assert status == rb.RB_OK
+        res[kernels] = (x.cpu().numpy(), st)
+    for b in range(3):
+        # FP32 CG trajectories drift with round-off: iteration counts agree to a few percent
+        i0, i1 = int(res[0][1]["iters"][b]), int(res[1][1]["iters"][b])
+        assert abs(i0 - i1) <= max(2, 0.05 * i1)
+        truth = direct.sparse_direct(prob, mu[b])
+        assert _rel(res[0][0][b], truth) < 1e-9
+    # one preconditioner application, point by point: fused vs one-sweep kernels (FP32 round-off)
+    r = np.random.default_rng(2).standard_normal((3, prob.n_dof)).astype(np.float32)
+    y_f = ctx.precondition(mu, r, precision="mixed", nu=nu, kernels=1, gemm="cuda_cores")
+    y_1 = ctx.precondition(mu, r, precision="mixed", nu=nu, kernels=0, gemm="cuda_cores")
+    assert np.abs(y_f - y_1).max() <= 1e-5 * np.abs(y_1).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,blocks,nu", [((40, 36), (3, 3), 1), ((128, 40), (3, 2), 3), ((14, 12, 10), (2, 2, 2), 2)])
+def test_preconditioner_matches_oracle(dims, blocks, nu):
+    """y = RBI(A(mu), r, W, 1) (eqs. 5-8) against the oracle's: FP64 to round-off, the mixed
+    engine (FP32 smoother, TF32 or FP32 products) to single-precision level."""
+    w = wl.small(dims, blocks, n_basis=6, n_train=24, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(2)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=2)
+    r = np.random.default_rng(9).standard_normal((2, prob.n_dof))
+    ref = np.stack([orb.rbi_precondition(basis, mu[b], orb.reduced_factor(basis, mu[b]), r[b], "rbgs", nu)
+                    for b in range(2)])
+    y64 = ctx.precondition(mu, r, precision="fp64", nu=nu)
+    assert np.abs(y64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    for gemm in ("cuda_cores", "auto"):
+        y32 = ctx.precondition(mu, r.astype(np.float32), precision="mixed", nu=nu, gemm=gemm)
+        tol = 1e-5 if gemm == "cuda_cores" else 3e-3
+        assert np.abs(y32 - ref).max() <= tol * np.abs(ref).max(), gemm
+    ctx.close()
+
+
 @pytest.mark.parametrize("dims,n", [((128, 96), 8), ((256, 33), 40), ((64, 64), 100)])
 def test_batched_products_both_engines(dims, n):
     """W^T R (eq. 5) and W E (eq. 7) against FP64 numpy: FP32 CUDA cores to 1e-5, TF32 tensor cores to
