@@ -25,6 +25,11 @@ sys.path.insert(0, ROOT)
 METRIC = "RB-PCG solves/sec to rel. residual 1e-10 (mixed+batched vs FP64 plain), % HBM roofline"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
 
+# DRAM bytes per grid point and query measured by ncu for the dominant kernel (small case,
+# profiles/rbcg_2d_512_smoother_dram.md); scaled to a full launch by its units.
+NCU_TRAFFIC = {("f32", "smooth"): {"intermediate": 11.4, "last": 17.0,
+                                   "source": "profiles/rbcg_2d_512_smoother_dram.md"}}
+
 # Algorithmic bytes per grid point per launch unit (one query, one pass), by kernel
 # and inner precision: every operand read or written once (eq. 5-8 and Alg. 3 steps).
 BYTES_PER_POINT = {
@@ -202,9 +207,11 @@ def main():
     offline_s = time.perf_counter() - t0
     _, _, _, _, sel = ctx.basis()
 
-    # weak scaling: every rank solves its own B test parameters
+    # weak scaling: every rank solves its own B test parameters (replicas, no data-path collective)
+    from paper_1804_06363_gb300.shard import max_over_ranks, shard_range
     mu_all = w.test_mu(B * world) if B * world <= w.n_test else w.draw_mu(w.test_seed, B * world)
-    mu = np.ascontiguousarray(mu_all[rank * B:(rank + 1) * B])
+    lo, hi = shard_range(B * world, rank, world)
+    mu = np.ascontiguousarray(mu_all[lo:hi])
     x = torch.zeros((B, N), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, stream=stream.cuda_stream)
@@ -238,13 +245,9 @@ def main():
     torch.cuda.synchronize()
     clocks = clk.stop()
     t_local = e0.elapsed_time(e1) / 1000.0
+    t_max = max_over_ranks(t_local, dist, dev)
     if world > 1:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
         dist.barrier()
-    else:
-        t_max = t_local
     value = world * B * args.steps / t_max
     last = stats[-1]
     ok = bool(np.all(last["status"] == rb.RB_OK))
@@ -288,10 +291,18 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     peak, peak_kind = measured_peaks()
     achieved = kernels[dom].get("gbs")
+    traffic = None
+    nt = NCU_TRAFFIC.get((prec, dom))
+    if nt is not None and dom == "smooth" and kernels[dom]["launches"]:
+        # one "smooth" launch = nu sweeps; bytes scaled to the average launch of this run
+        per_launch_units = iters / kernels[dom]["launches"]
+        traffic = round((nt["intermediate"] * (opts["nu"] - 1) + nt["last"]) * N * per_launch_units)
+    alg_per_launch = (kernels[dom].get("alg_bytes") or 0) / max(1, kernels[dom]["launches"])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
+                "traffic_source": nt["source"] if nt else None,
                 "peak_source": peak_kind,
-                "alg_bytes_per_unit": BYTES_PER_POINT[prec].get(dom),
+                "alg_bytes_per_unit": BYTES_PER_POINT[prec].get(dom), "alg_bytes_per_launch": round(alg_per_launch),
                 "unit_def": "one query x one grid point per launch"}
 
     # ---- end to end through the C interface with host buffers (pinned)
@@ -306,9 +317,7 @@ def main():
     e2e = {"value": world * B * args.steps / e2e_s if world == 1 else None, "unit": "solves/s",
            "h2d_bytes_per_step": int(mu.nbytes), "d2h_bytes_per_step": int(B * N * 8 + B * 24)}
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * B * args.steps / float(t.item())
+        e2e["value"] = world * B * args.steps / max_over_ranks(e2e_s, dist, dev)
 
     # ---- FP64 plain comparator (same GPU, same workload, fewer queries)
     fp64 = None
