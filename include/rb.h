@@ -83,8 +83,12 @@ typedef struct {
     int max_outer;      /* mixed: maximum FP64 refinement steps */
     int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
     int graph;          /* 1: replay the iteration body as a captured CUDA graph */
-    int kernels;        /* 0: one pass over memory per smoother sweep;
-                           1: all sweeps fused in one pass (FP32 mixed path, 2D, nu <= 6) */
+    int kernels;        /* smoother kernels (red-black Gauss-Seidel on 2D grids whose rows hold a
+                           multiple of 128 points; other cases always take the generic sweep):
+                           0: one pass over memory per sweep, rows staged in shared memory by
+                              bulk asynchronous copies;
+                           1: all sweeps fused in one pass (FP32 mixed path, nu <= 6);
+                           2: one pass per sweep, rows held in registers */
     void* stream;       /* cudaStream_t or NULL */
 } rb_opts;
 

@@ -403,6 +403,7 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bo
     P.lcnt = ctx->d_lcnt;
     P.lidx = ctx->d_lidx;
     P.ndone = ctx->d_ndone;
+    P.err = ctx->d_tcerr;
     P.tol = o.tol;
     P.inner_tol = o.inner_tol;
     P.max_iter = o.max_iter;
@@ -509,6 +510,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic &&
                 use_fused_smoother(ctx->geo, o.nu))
                 launch2d_smooth_fused(P, L, o.nu);
+            else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
+                launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
             else launch_smoother<float>(P, L, o.nu, false);
         });
@@ -517,7 +520,9 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
         timed(ctx, KK_RSOLVE, s, [&] { launch_reduced_solve<double>(P, L); });
         timed(ctx, KK_PROLONG, s, [&] { launch_prolong<double>(P, L, false); });
         timed(ctx, KK_SMOOTH, s, [&] {
-            if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
+            if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
+                launch2d_smooth_tma<double>(P, L, o.nu);
+            else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
             else launch_smoother<double>(P, L, o.nu, false);
         });
     }
@@ -526,7 +531,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
-        (o.kernels != 0 && o.kernels != 1) ||
+        (o.kernels < 0 || o.kernels > 2) ||
         (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED)) {
         ctx->err = "invalid options";
         return RB_EINVAL;
@@ -616,13 +621,13 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (rs != RB_OK) return rs;
-    if (use_tc) {
-        int tcerr = 0;
-        CK(cudaMemcpyAsync(&tcerr, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    {
+        int derr = 0;
+        CK(cudaMemcpyAsync(&derr, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (tcerr) {
+        if (derr) {
             cudaMemsetAsync(ctx->d_tcerr, 0, sizeof(int), s);
-            ctx->err = "a tensor-core kernel gave up waiting on its pipeline (device timeout)";
+            ctx->err = "a kernel gave up waiting on an asynchronous copy or MMA (device timeout)";
             return RB_ETIMEOUT;
         }
     }
@@ -945,11 +950,15 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             const double ms = trial(t);
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
-        if (best.smoother == RB_SMOOTH_RBGS && use_fused_smoother(ctx->geo, best.nu)) {
-            rb_opts t = best;
-            t.kernels = 1 - best.kernels;
-            const double ms = trial(t);
-            if (ms < best_ms) { best_ms = ms; best = t; }
+        if (best.smoother == RB_SMOOTH_RBGS && use_rowmarch(ctx->geo) && !ctx->force_generic) {
+            const rb_opts base = best;
+            for (int kk = 0; kk <= 2; ++kk) {
+                if (kk == base.kernels || (kk == 1 && !use_fused_smoother(ctx->geo, base.nu))) continue;
+                rb_opts t = base;
+                t.kernels = kk;
+                const double ms = trial(t);
+                if (ms < best_ms) { best_ms = ms; best = t; }
+            }
         }
     }
     cudaEventDestroy(e0);

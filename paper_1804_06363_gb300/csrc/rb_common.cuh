@@ -98,6 +98,7 @@ struct Params {
     int* lcnt;                   // [N_LISTS]
     int* lidx;                   // [N_LISTS][Bmax]
     int* ndone;                  // queries that reached PH_DONE
+    int* err;                    // raised by a kernel whose bounded wait expired
     // options
     double tol, inner_tol;
     int max_iter, max_outer;
@@ -260,6 +261,9 @@ bool use_rowmarch(const Geo& g);
 template <typename T> void launch2d_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch2d_cg_b(const Params& P, const Launch& L);
 template <typename T> void launch2d_smooth(const Params& P, const Launch& L, int nu);
+// one sweep per launch with rows staged in shared memory by bulk asynchronous copies
+bool use_tma_smoother(const Geo& g);
+template <typename T> void launch2d_smooth_tma(const Params& P, const Launch& L, int nu);
 // all nu sweeps in one pass (FP32, dim 2, mx even, nu <= 6)
 bool use_fused_smoother(const Geo& g, int nu);
 void launch2d_smooth_fused(const Params& P, const Launch& L, int nu);

@@ -14,7 +14,13 @@
 
 namespace rbk {
 
-constexpr int RB_ROWS = 32;   // rows per band
+#ifndef RB_BAND_ROWS
+#define RB_BAND_ROWS 32
+#endif
+#ifndef RB_MIN_BLOCKS
+#define RB_MIN_BLOCKS 1
+#endif
+constexpr int RB_ROWS = RB_BAND_ROWS;   // rows per band
 
 template <typename T> struct V4 { T v[4]; };
 
@@ -194,7 +200,7 @@ __device__ void finalize_prec2(const Params& P, int q, double ry, double apy) {
 // CG part A: p_new = y + beta p_old; accumulate p_new^T A p_new
 
 template <typename T>
-__global__ void __launch_bounds__(256) k2_cg_a(Params P) {
+__global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_cg_a(Params P) {
     __shared__ T mus[MAX_MU];
     __shared__ T sx[64], sw[64];
     __shared__ double red[32];
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(256) k2_cg_a(Params P) {
 // CG part B: d += alpha p; r_new = r_old - alpha A p; accumulate ||r_new||^2
 
 template <typename T>
-__global__ void __launch_bounds__(256) k2_cg_b(Params P) {
+__global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_cg_b(Params P) {
     __shared__ T mus[MAX_MU];
     __shared__ T sx[64], sw[64];
     __shared__ double red[32];
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(256) k2_cg_b(Params P) {
 // those are recomputed (never read from another CTA's output).
 
 template <typename T, bool LAST>
-__global__ void __launch_bounds__(256) k2_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
+__global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
     __shared__ T mus[MAX_MU];
     __shared__ T sx[3][64], sw[3][64];
     __shared__ double red[32];

@@ -238,6 +238,42 @@ def test_fused_smoother_matches_one_sweep_kernels(dims, blocks, nu):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,blocks,nu,B,check", [((128, 300), (3, 3), 2, 3, (0, 1, 2)),
+                                                    ((1024, 200), (2, 2), 1, 160, (0, 97, 159))])
+def test_staged_smoother_matches_register_kernels_and_oracle(dims, blocks, nu, B, check):
+    """The one-sweep smoother with rows staged in shared memory by bulk copies
+    (kernels=0) against the register row-march sweep (kernels=2) and the oracle's
+    RBI preconditioner (eqs. 5-8): bands of 128 rows with a ragged last band, and
+    (second case) more band work items than resident CTAs, so one CTA's row rings
+    carry over from item to item."""
+    w = wl.small(dims, blocks, n_basis=4 if B > 3 else 6, n_train=6 if B > 3 else 24, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(B)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=B)
+    r = np.random.default_rng(5).standard_normal((B, prob.n_dof))
+    y0 = ctx.precondition(mu, r, precision="fp64", nu=nu, kernels=0)
+    y2 = ctx.precondition(mu, r, precision="fp64", nu=nu, kernels=2)
+    assert np.abs(y0 - y2).max() <= 1e-13 * np.abs(y2).max()
+    for b in check:
+        ref = orb.rbi_precondition(basis, mu[b], orb.reduced_factor(basis, mu[b]), r[b], "rbgs", nu)
+        assert np.abs(y0[b] - ref).max() <= 1e-12 * np.abs(ref).max(), b
+    r32 = r.astype(np.float32)
+    z0 = ctx.precondition(mu, r32, precision="mixed", nu=nu, kernels=0, gemm="cuda_cores")
+    z2 = ctx.precondition(mu, r32, precision="mixed", nu=nu, kernels=2, gemm="cuda_cores")
+    assert np.abs(z0 - z2).max() <= 1e-6 * np.abs(z2).max()
+    if B <= 3:
+        # Polak-Ribiere beta from the smoother's fused (A p)^T y reduction: oracle iterations
+        x = torch.zeros((B, prob.n_dof), dtype=torch.float64, device="cuda")
+        status, st = ctx.pcg(mu, x, precision="fp64", nu=nu, kernels=0)
+        assert status == rb.RB_OK
+        for b in range(B):
+            ref = orb.rbcg(basis, mu[b], tol=1e-10, beta="pr", nu=nu)
+            assert abs(int(st["iters"][b]) - ref.iters) <= 2, (st[b], ref.iters)
+            assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9
+    ctx.close()
+
+
 @pytest.mark.parametrize("dims,blocks,nu", [((40, 36), (3, 3), 1), ((128, 40), (3, 2), 3), ((14, 12, 10), (2, 2, 2), 2)])
 def test_preconditioner_matches_oracle(dims, blocks, nu):
     """y = RBI(A(mu), r, W, 1) (eqs. 5-8) against the oracle's: FP64 to round-off, the mixed
