@@ -83,12 +83,13 @@ typedef struct {
     int max_outer;      /* mixed: maximum FP64 refinement steps */
     int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
     int graph;          /* 1: replay the iteration body as a captured CUDA graph */
-    int kernels;        /* smoother kernels (red-black Gauss-Seidel on 2D grids whose rows hold a
-                           multiple of 128 points; other cases always take the generic sweep):
-                           0: one pass over memory per sweep, rows staged in shared memory by
-                              bulk asynchronous copies;
-                           1: all sweeps fused in one pass (FP32 mixed path, nu <= 6);
-                           2: one pass per sweep, rows held in registers */
+    int kernels;        /* stencil kernels on 2D grids whose rows hold a multiple of 128 points
+                           (other grids always take the generic kernels):
+                           0: CG body and one smoother pass per sweep with rows staged in shared
+                              memory by bulk asynchronous copies;
+                           1: as 0, but all red-black sweeps fused in one pass (FP32 mixed path,
+                              nu <= 6);
+                           2: CG body and one smoother pass per sweep with rows held in registers */
     void* stream;       /* cudaStream_t or NULL */
 } rb_opts;
 

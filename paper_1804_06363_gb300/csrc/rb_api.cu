@@ -482,12 +482,29 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
     cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
     enqueue_prec(ctx, P, L, o, m, use_tc);
     cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
+    const bool staged = rm && o.kernels != 2 && use_staged_cg(ctx->geo);
     if (m.mixed) {
-        timed(ctx, KK_CG_A, s, [&] { if (rm) launch2d_cg_a<float>(P, L); else launch_cg_a<float>(P, L); });
-        timed(ctx, KK_CG_B, s, [&] { if (rm) launch2d_cg_b<float>(P, L); else launch_cg_b<float>(P, L); });
+        timed(ctx, KK_CG_A, s, [&] {
+            if (staged) launch2d_cg_a_staged<float>(P, L);
+            else if (rm) launch2d_cg_a<float>(P, L);
+            else launch_cg_a<float>(P, L);
+        });
+        timed(ctx, KK_CG_B, s, [&] {
+            if (staged) launch2d_cg_b_staged<float>(P, L);
+            else if (rm) launch2d_cg_b<float>(P, L);
+            else launch_cg_b<float>(P, L);
+        });
     } else {
-        timed(ctx, KK_CG_A, s, [&] { if (rm) launch2d_cg_a<double>(P, L); else launch_cg_a<double>(P, L); });
-        timed(ctx, KK_CG_B, s, [&] { if (rm) launch2d_cg_b<double>(P, L); else launch_cg_b<double>(P, L); });
+        timed(ctx, KK_CG_A, s, [&] {
+            if (staged) launch2d_cg_a_staged<double>(P, L);
+            else if (rm) launch2d_cg_a<double>(P, L);
+            else launch_cg_a<double>(P, L);
+        });
+        timed(ctx, KK_CG_B, s, [&] {
+            if (staged) launch2d_cg_b_staged<double>(P, L);
+            else if (rm) launch2d_cg_b<double>(P, L);
+            else launch_cg_b<double>(P, L);
+        });
     }
     cudaMemsetAsync(ctx->d_lcnt + L_ITER, 0, sizeof(int), s);
 }

@@ -212,6 +212,38 @@ __device__ __forceinline__ void finalize_prec_state(const Params& P, int q, doub
     list_push(P, L_ITER, q);
 }
 
+// CG part A finalizer: pap = p^T A p of the new direction; alpha = rho / pap (Alg. 3 step 5).
+__device__ __forceinline__ void finalize_cg_a_state(const Params& P, int q, double pap) {
+    QState& s = P.st[q];
+    if (!(pap > 0.0)) {
+        mark_done(P, s, RB_EBREAKDOWN);
+        return;
+    }
+    s.alpha = s.rho / pap;
+    s.ppar ^= 1;
+}
+
+// CG part B finalizer: rr = ||r_{k+1}||^2 of the recurrence residual (Alg. 3 step 8).
+// Below the cycle's target (or out of iterations) the query goes to the outer
+// residual check, else to the next preconditioner application.
+__device__ __forceinline__ void finalize_cg_b_state(const Params& P, int q, double rr) {
+    QState& s = P.st[q];
+    const double rn = sqrt(rr);
+    s.rnorm = rn;
+    s.iters += 1;
+    if (!(rn == rn)) {
+        mark_done(P, s, RB_EBREAKDOWN);
+        return;
+    }
+    if (rn < s.target || s.iters >= P.max_iter) {
+        s.phase = PH_OUTER;
+        list_push(P, L_OUT, q);
+    } else {
+        s.phase = PH_PREC;
+        list_push(P, L_PREC, q);
+    }
+}
+
 // Thread 0 publishes a CTA's partial sums for (q, tile); returns true in every
 // thread of the CTA that is the last to do so for q.  The caller then reduces
 // the partials in a fixed order (deterministic) and resets tick[q].
@@ -261,6 +293,10 @@ bool use_rowmarch(const Geo& g);
 template <typename T> void launch2d_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch2d_cg_b(const Params& P, const Launch& L);
 template <typename T> void launch2d_smooth(const Params& P, const Launch& L, int nu);
+// CG body with rows staged in shared memory by bulk asynchronous copies
+bool use_staged_cg(const Geo& g);
+template <typename T> void launch2d_cg_a_staged(const Params& P, const Launch& L);
+template <typename T> void launch2d_cg_b_staged(const Params& P, const Launch& L);
 // one sweep per launch with rows staged in shared memory by bulk asynchronous copies
 bool use_tma_smoother(const Geo& g);
 template <typename T> void launch2d_smooth_tma(const Params& P, const Launch& L, int nu);

@@ -212,13 +212,7 @@ __global__ void __launch_bounds__(THREADS) k_cg_a(Params P) {
             double tot;
             gather_partials(P, q, ntiles, 1, &tot, red);
             if (threadIdx.x == 0) {
-                QState& sw = P.st[q];
-                if (!(tot > 0.0)) {
-                    mark_done(P, sw, RB_EBREAKDOWN);
-                } else {
-                    sw.alpha = sw.rho / tot;
-                    sw.ppar ^= 1;
-                }
+                finalize_cg_a_state(P, q, tot);
                 P.tick[q] = 0;
             }
         }
@@ -226,21 +220,6 @@ __global__ void __launch_bounds__(THREADS) k_cg_a(Params P) {
 }
 
 // CG body, part B: d += alpha p, r_new = r_old - alpha A p, ||r_new||^2  (steps 6-8)
-
-__device__ void finalize_cg_b(const Params& P, int q, double rr) {
-    QState& s = P.st[q];
-    const double rn = sqrt(rr);
-    s.rnorm = rn;
-    s.iters += 1;
-    if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
-    if (rn < s.target || s.iters >= P.max_iter) {
-        s.phase = PH_OUTER;
-        list_push(P, L_OUT, q);
-    } else {
-        s.phase = PH_PREC;
-        list_push(P, L_PREC, q);
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
@@ -281,7 +260,7 @@ __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
             double tot;
             gather_partials(P, q, ntiles, 1, &tot, red);
             if (threadIdx.x == 0) {
-                finalize_cg_b(P, q, tot);
+                finalize_cg_b_state(P, q, tot);
                 P.tick[q] = 0;
             }
         }
@@ -301,22 +280,6 @@ __global__ void __launch_bounds__(THREADS) k_cg_b(Params P) {
 // Mode RBI: b = f(mu) in FP64, output x (last sweep) and no dot products.
 
 enum { SM_NONE = 0, SM_RBGS = 1, SM_JACOBI = 2 };
-
-// ry = r_{k+1}^T y_{k+1}; apy = (A p_k)^T y_{k+1}.  Polak-Ribiere:
-// y_{k+1}^T (r_{k+1} - r_k) = -alpha_k (A p_k)^T y_{k+1} since r_{k+1} = r_k - alpha_k A p_k.
-__device__ void finalize_prec(const Params& P, int q, double ry, double apy) {
-    QState& s = P.st[q];
-    if (!(ry > 0.0)) { mark_done(P, s, RB_EBREAKDOWN); return; }
-    if (s.start) {
-        s.beta = 0.0;
-        s.start = 0;
-    } else {
-        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : -s.alpha * apy / s.rho;
-    }
-    s.rho = ry;
-    s.phase = PH_ITER;
-    list_push(P, L_ITER, q);
-}
 
 template <typename T, int DIM, int KIND, bool RBI, bool LAST>
 __global__ void __launch_bounds__(THREADS) k_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
@@ -437,7 +400,7 @@ __global__ void __launch_bounds__(THREADS) k_smooth(Params P, const T* __restric
                     if constexpr (RBI) {
                         list_push(P, L_OUT, q);
                     } else {
-                        finalize_prec(P, q, tot[0], tot[1]);
+                        finalize_prec_state(P, q, tot[0], tot[1]);
                     }
                     P.tick[q] = 0;
                 }

@@ -166,36 +166,6 @@ __device__ __forceinline__ V4<T> apply_row(const RowCoef<T>& c, const V4<T>& vm,
     return out;
 }
 
-__device__ void finalize_cg_b2(const Params& P, int q, double rr) {
-    QState& s = P.st[q];
-    const double rn = sqrt(rr);
-    s.rnorm = rn;
-    s.iters += 1;
-    if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
-    if (rn < s.target || s.iters >= P.max_iter) {
-        s.phase = PH_OUTER;
-        list_push(P, L_OUT, q);
-    } else {
-        s.phase = PH_PREC;
-        list_push(P, L_PREC, q);
-    }
-}
-
-// Polak-Ribiere: y_{k+1}^T (r_{k+1} - r_k) = -alpha_k (A p_k)^T y_{k+1}
-__device__ void finalize_prec2(const Params& P, int q, double ry, double apy) {
-    QState& s = P.st[q];
-    if (!(ry > 0.0)) { mark_done(P, s, RB_EBREAKDOWN); return; }
-    if (s.start) {
-        s.beta = 0.0;
-        s.start = 0;
-    } else {
-        s.beta = (P.beta_form == RB_BETA_FR) ? ry / s.rho : -s.alpha * apy / s.rho;
-    }
-    s.rho = ry;
-    s.phase = PH_ITER;
-    list_push(P, L_ITER, q);
-}
-
 // ---------------------------------------------------------------------------
 // CG part A: p_new = y + beta p_old; accumulate p_new^T A p_new
 
@@ -263,9 +233,7 @@ __global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_cg_a(Params P) {
             double tot;
             gather_partials(P, q, nband, 1, &tot, red);
             if (threadIdx.x == 0) {
-                QState& sw2 = P.st[q];
-                if (!(tot > 0.0)) mark_done(P, sw2, RB_EBREAKDOWN);
-                else { sw2.alpha = sw2.rho / tot; sw2.ppar ^= 1; }
+                finalize_cg_a_state(P, q, tot);
                 P.tick[q] = 0;
             }
         }
@@ -337,7 +305,7 @@ __global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_cg_b(Params P) {
             double tot;
             gather_partials(P, q, nband, 1, &tot, red);
             if (threadIdx.x == 0) {
-                finalize_cg_b2(P, q, tot);
+                finalize_cg_b_state(P, q, tot);
                 P.tick[q] = 0;
             }
         }
@@ -483,7 +451,7 @@ __global__ void __launch_bounds__(256, RB_MIN_BLOCKS) k2_smooth(Params P, const 
                 double tot[2];
                 gather_partials(P, q, nband, 2, tot, red);
                 if (threadIdx.x == 0) {
-                    finalize_prec2(P, q, tot[0], tot[1]);
+                    finalize_prec_state(P, q, tot[0], tot[1]);
                     P.tick[q] = 0;
                 }
             }
