@@ -66,6 +66,7 @@ struct rb_ctx {
     int* d_lcnt = nullptr;
     int* d_lidx = nullptr;
     int* d_ndone = nullptr;
+    int* d_done = nullptr;            // finished queries in finishing order
     double* d_scratch = nullptr;      // offline helpers
     size_t scratch_bytes = 0;
     TcPlan tc{};                      // tensor-core projection plans
@@ -82,7 +83,9 @@ struct rb_ctx {
     // host
     QState* h_st = nullptr;
     int* h_ndone = nullptr;
+    int* h_done = nullptr;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // solutions of finished queries to host buffers
     int num_sms = 1;
     int grid = 1;
     std::string err;
@@ -271,6 +274,7 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     TRY(dalloc(ctx, &ctx->d_lcnt, N_LISTS));
     TRY(dalloc(ctx, &ctx->d_lidx, (size_t)N_LISTS * B));
     TRY(dalloc(ctx, &ctx->d_ndone, 1));
+    TRY(dalloc(ctx, &ctx->d_done, B));
     ctx->scratch_bytes = std::max<size_t>((size_t)128 * 128 * 128 * sizeof(double), 4096);
     TRY(dalloc(ctx, &ctx->d_scratch, ctx->scratch_bytes / sizeof(double)));
     TRY(dalloc(ctx, &ctx->d_tcerr, 1));
@@ -279,7 +283,9 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
                 ctx->d_W32r, ctx->d_tcerr, ctx->err));
 
     if (cudaMallocHost((void**)&ctx->h_st, (size_t)B * sizeof(QState)) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->h_ndone, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost((void**)&ctx->h_ndone, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_done, (size_t)B * sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "pinned host allocation failed";
         return RB_ENOMEM;
@@ -296,6 +302,8 @@ void ctx_destroy(rb_ctx* ctx) {
     ctx->allocs.clear();
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_ndone) cudaFreeHost(ctx->h_ndone);
+    if (ctx->h_done) cudaFreeHost(ctx->h_done);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -403,6 +411,7 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bo
     P.lcnt = ctx->d_lcnt;
     P.lidx = ctx->d_lidx;
     P.ndone = ctx->d_ndone;
+    P.done = ctx->d_done;
     P.err = ctx->d_tcerr;
     P.tol = o.tol;
     P.inner_tol = o.inner_tol;
@@ -473,11 +482,18 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
         cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
         return;
     }
+    const bool staged_outer = rm && o.kernels != 2 && use_staged_outer(ctx->geo);
     if (m.mixed) {
         timed(ctx, KK_OUTER_UPDATE, s, [&] { launch_outer_update(P, L); });
-        timed(ctx, KK_OUTER_RES, s, [&] { launch_outer_residual<float>(P, L); });
+        timed(ctx, KK_OUTER_RES, s, [&] {
+            if (staged_outer) launch2d_outer_residual_staged<float>(P, L);
+            else launch_outer_residual<float>(P, L);
+        });
     } else {
-        timed(ctx, KK_OUTER_RES, s, [&] { launch_outer_residual<double>(P, L); });
+        timed(ctx, KK_OUTER_RES, s, [&] {
+            if (staged_outer) launch2d_outer_residual_staged<double>(P, L);
+            else launch_outer_residual<double>(P, L);
+        });
     }
     cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
     enqueue_prec(ctx, P, L, o, m, use_tc);
@@ -556,9 +572,11 @@ rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     return RB_OK;
 }
 
-// Solve one wave of B <= Bmax queries; x64 is a device array [B][N].
+// Solve one wave of B <= Bmax queries; x64 is a device array [B][N].  With x_host
+// (host [B][N]) the solution of every query is copied there as soon as the query
+// finishes, on a side stream, while the others still iterate.
 rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool x_given, const rb_opts& o, Mode m,
-                   rb_stats* stats) {
+                   rb_stats* stats, double* x_host) {
     cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
     const long long N = ctx->N;
     for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i) {
@@ -617,6 +635,15 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
     const long long max_steps = (long long)o.max_iter + 2LL * o.max_outer + 64;
     long long steps = 0;
     rb_status rs = RB_OK;
+    int copied = 0;   // finished queries whose solution copy to x_host is issued
+    auto copy_finished = [&](int upto) {
+        for (; copied < upto; ++copied) {
+            const int q = ctx->h_done[copied];
+            if (q < 0 || q >= B) continue;
+            cudaMemcpyAsync(x_host + (size_t)q * N, x64 + (size_t)q * N, (size_t)N * sizeof(double),
+                            cudaMemcpyDeviceToHost, ctx->copy_stream);
+        }
+    };
     for (;;) {
         if (exec) {
             cudaError_t e = cudaGraphLaunch(exec, s);
@@ -626,9 +653,11 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
         }
         steps += check_every;
         cudaMemcpyAsync(ctx->h_ndone, ctx->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (x_host) cudaMemcpyAsync(ctx->h_done, ctx->d_done, (size_t)B * sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { ctx->err = std::string("solve failed: ") + cudaGetErrorString(e); rs = RB_ECUDA; break; }
         if (ctx->profiling) flush_profile(ctx);
+        if (x_host) copy_finished(std::min(*ctx->h_ndone, B));
         if (*ctx->h_ndone >= B) break;
         if (steps > max_steps) {
             ctx->err = "solver state machine did not finish within its step budget";
@@ -637,6 +666,24 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
         }
     }
     if (exec) cudaGraphExecDestroy(exec);
+    if (x_host) {
+        // queries that never reached PH_DONE (a failed wave) still get their current iterate
+        if (rs != RB_OK) {
+            std::vector<char> seen(B, 0);
+            for (int i = 0; i < copied; ++i)
+                if (ctx->h_done[i] >= 0 && ctx->h_done[i] < B) seen[ctx->h_done[i]] = 1;
+            for (int q = 0; q < B; ++q)
+                if (!seen[q])
+                    cudaMemcpyAsync(x_host + (size_t)q * N, x64 + (size_t)q * N, (size_t)N * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+        }
+        const cudaError_t ce = cudaStreamSynchronize(ctx->copy_stream);
+        if (ce != cudaSuccess && rs == RB_OK) {
+            ctx->err = std::string("solution copy failed: ") + cudaGetErrorString(ce);
+            rs = RB_ECUDA;
+        }
+    }
     if (rs != RB_OK) return rs;
     {
         int derr = 0;
@@ -684,13 +731,10 @@ rb_status run_batch(rb_ctx* ctx, int B, const double* mu, double* x, const rb_op
         double* x64 = dev_x ? x + (size_t)b0 * N : ctx->d_x64;
         if (!dev_x && x_given)
             CK(cudaMemcpyAsync(x64, x + (size_t)b0 * N, (size_t)nbw * N * sizeof(double), cudaMemcpyHostToDevice, s));
-        rb_status w = run_wave(ctx, nbw, mu + (size_t)b0 * ctx->n_mu, x64, x_given, o, m, stats ? stats + b0 : nullptr);
+        rb_status w = run_wave(ctx, nbw, mu + (size_t)b0 * ctx->n_mu, x64, x_given, o, m, stats ? stats + b0 : nullptr,
+                               dev_x ? nullptr : x + (size_t)b0 * N);
         if (w == RB_EINVAL || w == RB_ECUDA || w == RB_ETIMEOUT) return w;
         if (w > worst) worst = w;
-        if (!dev_x) {
-            CK(cudaMemcpyAsync(x + (size_t)b0 * N, x64, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
     }
     return worst;
 }

@@ -98,6 +98,7 @@ struct Params {
     int* lcnt;                   // [N_LISTS]
     int* lidx;                   // [N_LISTS][Bmax]
     int* ndone;                  // queries that reached PH_DONE
+    int* done;                   // [Bmax] those queries in the order they finished (or null)
     int* err;                    // raised by a kernel whose bounded wait expired
     // options
     double tol, inner_tol;
@@ -192,7 +193,8 @@ __device__ __forceinline__ void list_push(const Params& P, int list, int q) {
 __device__ __forceinline__ void mark_done(const Params& P, QState& s, int status) {
     s.phase = PH_DONE;
     s.status = status;
-    atomicAdd(P.ndone, 1);
+    const int pos = atomicAdd(P.ndone, 1);
+    if (P.done) P.done[pos] = (int)(&s - P.st);
 }
 
 // Preconditioner finalizer: ry = r_{k+1}^T y_{k+1}, apy = (A p_k)^T y_{k+1}.
@@ -210,6 +212,34 @@ __device__ __forceinline__ void finalize_prec_state(const Params& P, int q, doub
     s.rho = ry;
     s.phase = PH_ITER;
     list_push(P, L_ITER, q);
+}
+
+// Outer (true-residual) finalizer: rr = ||f - A x||^2 in FP64, ff = ||f||^2.
+__device__ __forceinline__ void finalize_outer_state(const Params& P, int q, double rr, double ff) {
+    QState& s = P.st[q];
+    if (s.outer == 0) s.fnorm = sqrt(ff);
+    const double prev = s.rel_res;
+    s.outer += 1;
+    const double rn = sqrt(rr);
+    const double fn = s.fnorm > 0.0 ? s.fnorm : 1.0;
+    s.rel_res = rn / fn;
+    s.rnorm = rn;
+    s.xzero = 0;
+    if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
+    if (s.rel_res < P.tol) { mark_done(P, s, RB_OK); return; }
+    if (s.iters >= P.max_iter || s.outer > P.max_outer) { mark_done(P, s, RB_ENOCONV); return; }
+    // a full CG cycle that gained less than 10% on the true residual has hit
+    // the rounding floor of the FP64 residual: stop instead of cycling
+    if (s.outer > 2 && s.rel_res > 0.9 * prev) { mark_done(P, s, RB_ENOCONV); return; }
+    if (s.outer > 1 && !P.mixed) s.restarts += 1;
+    // mixed: each FP32 cycle reduces its own residual by inner_tol, but never
+    // aims below half the outer tolerance (the FP64 step then finishes).
+    // FP64: the first cycle stops at tol (Alg. 3 step 8); a restart after a
+    // failed true-residual check aims at half of it.
+    s.target = P.mixed ? fmax(P.inner_tol * rn, 0.5 * P.tol * fn) : (s.outer > 1 ? 0.5 : 1.0) * P.tol * fn;
+    s.phase = PH_PREC;
+    s.start = 1;
+    list_push(P, L_PREC, q);
 }
 
 // CG part A finalizer: pap = p^T A p of the new direction; alpha = rho / pap (Alg. 3 step 5).
@@ -293,6 +323,9 @@ bool use_rowmarch(const Geo& g);
 template <typename T> void launch2d_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch2d_cg_b(const Params& P, const Launch& L);
 template <typename T> void launch2d_smooth(const Params& P, const Launch& L, int nu);
+// FP64 outer residual with rows of x staged in shared memory by bulk asynchronous copies
+bool use_staged_outer(const Geo& g);
+template <typename TR> void launch2d_outer_residual_staged(const Params& P, const Launch& L);
 // CG body with rows staged in shared memory by bulk asynchronous copies
 bool use_staged_cg(const Geo& g);
 template <typename T> void launch2d_cg_a_staged(const Params& P, const Launch& L);

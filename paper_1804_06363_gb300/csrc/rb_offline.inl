@@ -76,7 +76,7 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
         const int n = ctx->n;
         // step 3: snapshot, RBCG with W_{n} (no basis when n = 0)
         rb_stats st;
-        rb_status ws = run_wave(ctx, 1, mu_train + (size_t)cand * n_mu, bb.snap, false, o, Mode{false, false}, &st);
+        rb_status ws = run_wave(ctx, 1, mu_train + (size_t)cand * n_mu, bb.snap, false, o, Mode{false, false}, &st, nullptr);
         // a snapshot that stalled at the FP64 residual floor within 10x the target is kept
         if (ws == RB_ENOCONV && st.rel_res < 10.0 * b.truth_tol) ws = RB_OK;
         if (ws != RB_OK) {

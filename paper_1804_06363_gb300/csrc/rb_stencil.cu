@@ -71,33 +71,6 @@ __device__ __forceinline__ double block_sum_d(T v, double* red) {
 // ----------------------------------------------------------------------------
 // outer residual r = f(mu) - A(mu) x  (FP64 arithmetic, stored as T)
 
-__device__ void finalize_outer(const Params& P, int q, double rr, double ff) {
-    QState& s = P.st[q];
-    if (s.outer == 0) s.fnorm = sqrt(ff);
-    const double prev = s.rel_res;
-    s.outer += 1;
-    const double rn = sqrt(rr);
-    const double fn = s.fnorm > 0.0 ? s.fnorm : 1.0;
-    s.rel_res = rn / fn;
-    s.rnorm = rn;
-    s.xzero = 0;
-    if (!(rn == rn)) { mark_done(P, s, RB_EBREAKDOWN); return; }
-    if (s.rel_res < P.tol) { mark_done(P, s, RB_OK); return; }
-    if (s.iters >= P.max_iter || s.outer > P.max_outer) { mark_done(P, s, RB_ENOCONV); return; }
-    // a full CG cycle that gained less than 10% on the true residual has hit
-    // the rounding floor of the FP64 residual: stop instead of cycling
-    if (s.outer > 2 && s.rel_res > 0.9 * prev) { mark_done(P, s, RB_ENOCONV); return; }
-    if (s.outer > 1 && !P.mixed) s.restarts += 1;
-    // mixed: each FP32 cycle reduces its own residual by inner_tol, but never
-    // aims below half the outer tolerance (the FP64 step then finishes).
-    // FP64: the first cycle stops at tol (Alg. 3 step 8); a restart after a
-    // failed true-residual check aims at half of it.
-    s.target = P.mixed ? fmax(P.inner_tol * rn, 0.5 * P.tol * fn) : (s.outer > 1 ? 0.5 : 1.0) * P.tol * fn;
-    s.phase = PH_PREC;
-    s.start = 1;
-    list_push(P, L_PREC, q);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_outer_residual(Params P) {
     __shared__ double mus[MAX_MU];
@@ -141,7 +114,7 @@ __global__ void __launch_bounds__(THREADS) k_outer_residual(Params P) {
             double tot[2];
             gather_partials(P, q, ntiles, 2, tot, red);
             if (threadIdx.x == 0) {
-                finalize_outer(P, q, tot[0], tot[1]);
+                finalize_outer_state(P, q, tot[0], tot[1]);
                 P.tick[q] = 0;
             }
         }
