@@ -36,7 +36,7 @@ struct rb_ctx {
     std::vector<rb_load> loads;
     int load_param[MAX_LOADS] = {0};
     Geo geo{};
-    int *d_bx = nullptr, *d_by = nullptr, *d_bz = nullptr;
+    int *d_bx = nullptr, *d_by = nullptr, *d_bz = nullptr, *d_rkey = nullptr;
     double* d_fr = nullptr;
     // basis
     int n = 0, n_cap = 0, nbp = 16, nbp32 = 32;
@@ -196,6 +196,14 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     CK(cudaMemcpy(ctx->d_bx, maps[0].data(), ctx->m[0] * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_by, maps[1].data(), ctx->m[1] * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_bz, maps[2].data(), ctx->m[2] * sizeof(int), cudaMemcpyHostToDevice));
+    {
+        std::vector<int> rk(ctx->m[1]);
+        const std::vector<int>& by = maps[1];
+        for (int k = 0; k < ctx->m[1]; ++k)
+            rk[k] = by[k] | ((k > 0 ? by[k - 1] : 0xFF) << 8) | ((k < ctx->m[1] - 1 ? by[k + 1] : 0xFF) << 16);
+        TRY(dalloc(ctx, &ctx->d_rkey, ctx->m[1]));
+        CK(cudaMemcpy(ctx->d_rkey, rk.data(), ctx->m[1] * sizeof(int), cudaMemcpyHostToDevice));
+    }
     Geo& g = ctx->geo;
     g.dim = ctx->dim;
     g.mx = ctx->m[0]; g.my = ctx->m[1]; g.mz = ctx->m[2];
@@ -205,7 +213,7 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     g.ihx2 = (double)(g.mx + 1) * (g.mx + 1);
     g.ihy2 = (double)(g.my + 1) * (g.my + 1);
     g.ihz2 = ctx->dim == 3 ? (double)(g.mz + 1) * (g.mz + 1) : 0.0;
-    g.bx = ctx->d_bx; g.by = ctx->d_by; g.bz = ctx->d_bz;
+    g.bx = ctx->d_bx; g.by = ctx->d_by; g.bz = ctx->d_bz; g.rkey = ctx->d_rkey;
 
     // load terms
     TRY(dalloc(ctx, &ctx->d_fr, (size_t)ctx->R * N));

@@ -12,6 +12,8 @@
 // (p row k+1; r and d rows k inside the band); step k applies A at row k from
 // the register window of p rows k-1 .. k+1 and the x neighbours read from the
 // staged p row k.
+//
+// Both read a stage in its own step and the next one (LAG 2).
 #include "rb_stage.cuh"
 
 namespace rbk {
@@ -23,6 +25,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
     __shared__ double red[32];
+    constexpr int LAG = 2;
     const Geo& g = P.g;
     const int mx = g.mx, my = g.my;
     const Layout<T> lay(mx, 2, 0);
@@ -35,10 +38,57 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
     const T* zero_row = reinterpret_cast<const T*>(g_zero_row);
     setup(lay, ring, bar, mx);
 
-    const int nband = (my + TB_ROWS - 1) / TB_ROWS;
     const int cnt = P.lcnt[L_ITER];
+    const int rows = band_rows(my, cnt, P.max_tiles);
+    const int nband = (my + rows - 1) / rows;
     const long long total = (long long)cnt * nband;
+
+    // producer cursor (shared memory; lane 0 of the producer warp only)
+    struct Cursor {
+        const T* yg;
+        const T* po;
+        long long w;
+        int y1, k;
+        unsigned issued;
+        bool use_old;
+    };
+    __shared__ Cursor cur;
+    auto cursor_item = [&](long long w) {
+        for (; w < total; w += gridDim.x) {   // skip the items of queries not in the CG body
+            const int slot = (int)(w / nband), band = (int)(w % nband);
+            const int q = P.lidx[L_ITER * P.Bmax + slot];
+            const QState& s = P.st[q];
+            if (s.phase != PH_ITER) continue;
+            cur.yg = reinterpret_cast<const T*>(P.y) + (size_t)q * g.n;
+            cur.po = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
+            const int y0 = band * rows;
+            cur.y1 = min(my, y0 + rows);
+            cur.k = y0 - 2;
+            cur.use_old = (T)s.beta != T(0);
+            break;
+        }
+        cur.w = w;
+    };
+    auto issue_next = [&]() {
+        if (cur.w >= total) return;
+        const unsigned u = cur.issued++;
+        T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
+        uint64_t* b = bar + u % RING;
+        const int m = cur.k + 1;
+        const bool in = m >= 0 && m < my;
+        mb_arrive_tx(b, row_bytes * (cur.use_old ? 2u : 1u));
+        bulk_row(sg, in ? cur.yg + (size_t)m * mx : zero_row, row_bytes, b);
+        if (cur.use_old) bulk_row(sg + lay.stride, in ? cur.po + (size_t)m * mx : zero_row, row_bytes, b);
+        if (++cur.k > cur.y1 - 1) cursor_item(cur.w + gridDim.x);
+    };
+    if (issuer) {
+        cur.issued = 0;
+        cursor_item(blockIdx.x);
+        for (int i = 0; i < RING; ++i) issue_next();
+    }
+
     unsigned seq = 0;
+    bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / nband), band = (int)(w % nband);
         const int q = P.lidx[L_ITER * P.Bmax + slot];
@@ -46,27 +96,11 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
         if (s.phase != PH_ITER) continue;   // uniform across the CTA
         const T beta = (T)s.beta;
         const bool use_old = beta != T(0);
-        const int y0 = band * TB_ROWS, y1 = min(my, y0 + TB_ROWS);
+        const int y0 = band * rows, y1 = min(my, y0 + rows);
         const int kfirst = y0 - 2, klast = y1 - 1;
-        const size_t base = (size_t)q * g.n;
-        const T* yg = reinterpret_cast<const T*>(P.y) + base;
-        const T* po = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
         T* pnew = reinterpret_cast<T*>(P.p) + ((size_t)q * 2 + (s.ppar ^ 1)) * g.n;
-        const uint32_t stage_bytes = row_bytes * (use_old ? 2u : 1u);
         __syncthreads();
         for (int j = threadIdx.x; j < P.n_mu; j += blockDim.x) mus[j] = (T)P.mu[(size_t)q * P.n_mu + j];
-        auto issue = [&](int kk) {
-            const unsigned u = seq + (unsigned)(kk - kfirst);
-            T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
-            uint64_t* b = bar + u % RING;
-            mb_arrive_tx(b, stage_bytes);
-            const int m = kk + 1;
-            const bool in = m >= 0 && m < my;
-            bulk_row(sg, in ? yg + (size_t)m * mx : zero_row, row_bytes, b);
-            if (use_old) bulk_row(sg + lay.stride, in ? po + (size_t)m * mx : zero_row, row_bytes, b);
-        };
-        if (issuer)
-            for (int kk = kfirst; kk <= klast && kk < kfirst + RING; ++kk) issue(kk);
         __syncthreads();
 
         T vm[4], vc[4], vp[4];   // p_new rows k-1, k, k+1
@@ -74,8 +108,8 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
         for (int j = 0; j < 4; ++j) vm[j] = vc[j] = vp[j] = T(0);
         TCoef<T> c;
         int key = -1;
+        int kpf = __ldg(g.rkey + y0);
         T acc = T(0);
-        bool ok = true;
         unsigned cslot = seq % RING, cpar = (seq / RING) & 1u;
         for (int k = kfirst; k <= klast; ++k) {
             if (!producer) {
@@ -96,31 +130,32 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
                     vp[j] = a.v[j];
                 }
                 if (k >= y0) {
+                    const int kk = kpf;
+                    kpf = __ldg(g.rkey + min(k + 1, my - 1));
+                    if (kk != key) {
+                        tcoef<T>(g, mus, x0, k, c);
+                        key = kk;
+                    }
                     // x neighbours of row k, formed like the neighbour threads form them
                     T left = sprev[x0 - 1], right = sprev[x0 + 4];
                     if (use_old) {
                         left += beta * sprev[lay.stride + x0 - 1];
                         right += beta * sprev[lay.stride + x0 + 4];
                     }
-                    const int kk = tkey(g, k);
-                    if (kk != key) {
-                        tcoef<T>(g, mus, x0, k, c);
-                        key = kk;
-                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc += vc[j] * apply_pt(c, j, vm, vc, vp, left, right);
                 }
             }
             __syncthreads();
-            if (issuer && k - 2 >= kfirst && k - 2 + RING <= klast) issue(k - 2 + RING);
+            if (issuer && seq >= (unsigned)LAG) issue_next();
+            ++seq;
             if (++cslot == RING) {
                 cslot = 0;
                 cpar ^= 1u;
             }
         }
-        seq += (unsigned)(klast - kfirst + 1);
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, seq);
+            if (issuer) drain(bar, cur.issued);
             __syncthreads();
             return;
         }
@@ -142,6 +177,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
     __shared__ double red[32];
+    constexpr int LAG = 2;
     const Geo& g = P.g;
     const int mx = g.mx, my = g.my;
     const Layout<T> lay(mx, 3, 0);
@@ -154,39 +190,73 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
     const T* zero_row = reinterpret_cast<const T*>(g_zero_row);
     setup(lay, ring, bar, mx);
 
-    const int nband = (my + TB_ROWS - 1) / TB_ROWS;
     const int cnt = P.lcnt[L_ITER];
+    const int rows = band_rows(my, cnt, P.max_tiles);
+    const int nband = (my + rows - 1) / rows;
     const long long total = (long long)cnt * nband;
+
+    struct Cursor {
+        const T* pg;
+        const T* rg;
+        const T* dg;
+        long long w;
+        int y0, y1, k;
+        unsigned issued;
+    };
+    __shared__ Cursor cur;
+    auto cursor_item = [&](long long w) {
+        for (; w < total; w += gridDim.x) {
+            const int slot = (int)(w / nband), band = (int)(w % nband);
+            const int q = P.lidx[L_ITER * P.Bmax + slot];
+            const QState& s = P.st[q];
+            if (s.phase != PH_ITER) continue;
+            const size_t base = (size_t)q * g.n;
+            cur.pg = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
+            cur.rg = reinterpret_cast<const T*>(P.r) + base;
+            cur.dg = (P.mixed ? reinterpret_cast<const T*>(P.d) : reinterpret_cast<const T*>(P.x64)) + base;
+            cur.y0 = band * rows;
+            cur.y1 = min(my, cur.y0 + rows);
+            cur.k = cur.y0 - 2;
+            break;
+        }
+        cur.w = w;
+    };
+    auto issue_next = [&]() {
+        if (cur.w >= total) return;
+        const unsigned u = cur.issued++;
+        T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
+        uint64_t* b = bar + u % RING;
+        const int kk = cur.k, m = kk + 1;
+        const bool rows_rd = kk >= cur.y0;   // r and d rows of the band (kk < y1 always)
+        mb_arrive_tx(b, row_bytes * (rows_rd ? 3u : 1u));
+        bulk_row(sg, (m >= 0 && m < my) ? cur.pg + (size_t)m * mx : zero_row, row_bytes, b);
+        if (rows_rd) {
+            bulk_row(sg + lay.stride, cur.dg + (size_t)kk * mx, row_bytes, b);
+            bulk_row(sg + 2 * lay.stride, cur.rg + (size_t)kk * mx, row_bytes, b);
+        }
+        if (++cur.k > cur.y1 - 1) cursor_item(cur.w + gridDim.x);
+    };
+    if (issuer) {
+        cur.issued = 0;
+        cursor_item(blockIdx.x);
+        for (int i = 0; i < RING; ++i) issue_next();
+    }
+
     unsigned seq = 0;
+    bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / nband), band = (int)(w % nband);
         const int q = P.lidx[L_ITER * P.Bmax + slot];
         const QState& s = P.st[q];
         if (s.phase != PH_ITER) continue;   // uniform across the CTA
         const T alpha = (T)s.alpha;
-        const int y0 = band * TB_ROWS, y1 = min(my, y0 + TB_ROWS);
+        const int y0 = band * rows, y1 = min(my, y0 + rows);
         const int kfirst = y0 - 2, klast = y1 - 1;
         const size_t base = (size_t)q * g.n;
-        const T* pg = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
         T* rg = reinterpret_cast<T*>(P.r) + base;
         T* dg = (P.mixed ? reinterpret_cast<T*>(P.d) : reinterpret_cast<T*>(P.x64)) + base;
         __syncthreads();
         for (int j = threadIdx.x; j < P.n_mu; j += blockDim.x) mus[j] = (T)P.mu[(size_t)q * P.n_mu + j];
-        auto issue = [&](int kk) {
-            const unsigned u = seq + (unsigned)(kk - kfirst);
-            T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
-            uint64_t* b = bar + u % RING;
-            const bool rows = kk >= y0;   // r and d rows of the band (kk < y1 always)
-            mb_arrive_tx(b, row_bytes * (rows ? 3u : 1u));
-            const int m = kk + 1;
-            bulk_row(sg, (m >= 0 && m < my) ? pg + (size_t)m * mx : zero_row, row_bytes, b);
-            if (rows) {
-                bulk_row(sg + lay.stride, dg + (size_t)kk * mx, row_bytes, b);
-                bulk_row(sg + 2 * lay.stride, rg + (size_t)kk * mx, row_bytes, b);
-            }
-        };
-        if (issuer)
-            for (int kk = kfirst; kk <= klast && kk < kfirst + RING; ++kk) issue(kk);
         __syncthreads();
 
         T vm[4], vc[4], vp[4];   // p rows k-1, k, k+1
@@ -194,8 +264,8 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
         for (int j = 0; j < 4; ++j) vm[j] = vc[j] = vp[j] = T(0);
         TCoef<T> c;
         int key = -1;
+        int kpf = __ldg(g.rkey + y0);
         T acc = T(0);
-        bool ok = true;
         unsigned cslot = seq % RING, cpar = (seq / RING) & 1u;
         for (int k = kfirst; k <= klast; ++k) {
             if (!producer) {
@@ -210,12 +280,13 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
                     vp[j] = a.v[j];
                 }
                 if (k >= y0) {
-                    const T left = sprev[x0 - 1], right = sprev[x0 + 4];   // p row k
-                    const int kk = tkey(g, k);
+                    const int kk = kpf;
+                    kpf = __ldg(g.rkey + min(k + 1, my - 1));
                     if (kk != key) {
                         tcoef<T>(g, mus, x0, k, c);
                         key = kk;
                     }
+                    const T left = sprev[x0 - 1], right = sprev[x0 + 4];   // p row k
                     const V4t<T> dk = lds4(sg + lay.stride + x0);
                     const V4t<T> rk = lds4(sg + 2 * lay.stride + x0);
                     V4t<T> dn, rn;
@@ -231,15 +302,15 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
                 }
             }
             __syncthreads();
-            if (issuer && k - 2 >= kfirst && k - 2 + RING <= klast) issue(k - 2 + RING);
+            if (issuer && seq >= (unsigned)LAG) issue_next();
+            ++seq;
             if (++cslot == RING) {
                 cslot = 0;
                 cpar ^= 1u;
             }
         }
-        seq += (unsigned)(klast - kfirst + 1);
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, seq);
+            if (issuer) drain(bar, cur.issued);
             __syncthreads();
             return;
         }

@@ -34,6 +34,8 @@ struct Geo {
     const int* bx;               // block index along x of every node column, [mx]
     const int* by;               // [my]
     const int* bz;               // [mz]
+    const int* rkey;             // [my] block rows of y-rows k-1, k, k+1 packed (0xFF: no row); rows
+                                 // with equal keys have equal face coefficients in 2D
 };
 
 // Per-query phase of the solver state machine.

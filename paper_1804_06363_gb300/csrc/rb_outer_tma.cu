@@ -4,7 +4,7 @@
 // and ||r||^2, ||f||^2 go to the outer finalizer (Alg. 3 step 8 on the true
 // residual).
 //
-// Step k (k = y0-2 .. y1-1) consumes stage k = x row k+1 and, for rows of the
+// Step k (k = y0-2 .. y1-1) consumes stage k = x row k+1 (LAG 2) and, for rows of the
 // band, forms f(mu) = sum_r phi_r(mu) f_r at the thread's 4 points (eq. 3; the
 // load vectors stay in L2 across queries) and A x from the register window of
 // x rows k-1 .. k+1 with the face coefficients cached per row key.  FP64 runs
@@ -34,33 +34,64 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
     const double* zero_row = g_zero_row;
     setup(lay, ring, bar, mx);
 
-    const int nband = (my + TB_ROWS - 1) / TB_ROWS;
     const int cnt = P.lcnt[L_OUT];
+    const int rows = band_rows(my, cnt, P.max_tiles);
+    const int nband = (my + rows - 1) / rows;
     const long long total = (long long)cnt * nband;
+    constexpr int LAG = 2;
+
+    // producer cursor (shared memory; lane 0 of the producer warp only).  Items of
+    // queries that start from x = 0 have no stages.
+    struct Cursor {
+        const double* xg;
+        long long w;
+        int y1, k;
+        unsigned issued;
+    };
+    __shared__ Cursor cur;
+    auto cursor_item = [&](long long w) {
+        for (; w < total; w += gridDim.x) {
+            const int slot = (int)(w / nband), band = (int)(w % nband);
+            const int q = P.lidx[L_OUT * P.Bmax + slot];
+            const QState& s = P.st[q];
+            if (s.phase == PH_DONE || s.xzero) continue;
+            cur.xg = P.x64 + (size_t)q * g.n;
+            const int y0 = band * rows;
+            cur.y1 = min(my, y0 + rows);
+            cur.k = y0 - 2;
+            break;
+        }
+        cur.w = w;
+    };
+    auto issue_next = [&]() {
+        if (cur.w >= total) return;
+        const unsigned u = cur.issued++;
+        double* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
+        uint64_t* b = bar + u % RING;
+        const int m = cur.k + 1;
+        mb_arrive_tx(b, row_bytes);
+        bulk_row(sg, (m >= 0 && m < my) ? cur.xg + (size_t)m * mx : zero_row, row_bytes, b);
+        if (++cur.k > cur.y1 - 1) cursor_item(cur.w + gridDim.x);
+    };
+    if (issuer) {
+        cur.issued = 0;
+        cursor_item(blockIdx.x);
+        for (int i = 0; i < RING; ++i) issue_next();
+    }
+
     unsigned seq = 0;
+    bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / nband), band = (int)(w % nband);
         const int q = P.lidx[L_OUT * P.Bmax + slot];
         const QState& s = P.st[q];
         if (s.phase == PH_DONE) continue;   // uniform across the CTA
         const bool xzero = s.xzero != 0;
-        const int y0 = band * TB_ROWS, y1 = min(my, y0 + TB_ROWS);
+        const int y0 = band * rows, y1 = min(my, y0 + rows);
         const int kfirst = y0 - 2, klast = y1 - 1;
-        const size_t base = (size_t)q * g.n;
-        const double* xg = P.x64 + base;
-        TR* rout = reinterpret_cast<TR*>(P.r) + base;
+        TR* rout = reinterpret_cast<TR*>(P.r) + (size_t)q * g.n;
         __syncthreads();
         for (int j = threadIdx.x; j < P.n_mu; j += blockDim.x) mus[j] = P.mu[(size_t)q * P.n_mu + j];
-        auto issue = [&](int kk) {
-            const unsigned u = seq + (unsigned)(kk - kfirst);
-            double* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
-            uint64_t* b = bar + u % RING;
-            mb_arrive_tx(b, row_bytes);
-            const int m = kk + 1;
-            bulk_row(sg, (m >= 0 && m < my) ? xg + (size_t)m * mx : zero_row, row_bytes, b);
-        };
-        if (issuer && !xzero)
-            for (int kk = kfirst; kk <= klast && kk < kfirst + RING; ++kk) issue(kk);
         __syncthreads();
         double phi[8];
 #pragma unroll
@@ -82,7 +113,6 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
             }
         };
         double rr = 0.0, ff = 0.0;
-        bool ok = true;
         if (xzero) {
             if (!producer)
                 for (int k = y0; k < y1; ++k) {
@@ -103,6 +133,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
             for (int j = 0; j < 4; ++j) vm[j] = vc[j] = vp[j] = 0.0;
             TCoef<double> c;
             int key = -1;
+            int kpf = __ldg(g.rkey + y0);
             unsigned cslot = seq % RING, cpar = (seq / RING) & 1u;
             for (int k = kfirst; k <= klast; ++k) {
                 if (!producer) {
@@ -119,7 +150,8 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
                     }
                     if (k >= y0) {
                         const double left = sprev[x0 - 1], right = sprev[x0 + 4];   // x row k
-                        const int kk = tkey(g, k);
+                        const int kk = kpf;
+                        kpf = __ldg(g.rkey + min(k + 1, my - 1));
                         if (kk != key) {
                             tcoef<double>(g, mus, x0, k, c);
                             key = kk;
@@ -138,16 +170,16 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
                     }
                 }
                 __syncthreads();
-                if (issuer && k - 2 >= kfirst && k - 2 + RING <= klast) issue(k - 2 + RING);
+                if (issuer && seq >= (unsigned)LAG) issue_next();
+                ++seq;
                 if (++cslot == RING) {
                     cslot = 0;
                     cpar ^= 1u;
                 }
             }
-            seq += (unsigned)(klast - kfirst + 1);
         }
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, seq);
+            if (issuer) drain(bar, cur.issued);
             __syncthreads();
             return;
         }

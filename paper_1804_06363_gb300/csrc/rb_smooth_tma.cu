@@ -1,28 +1,28 @@
 // One red-black Gauss-Seidel sweep (eq. 8) on 2D grids, with the rows staged in
-// shared memory by bulk asynchronous copies (cp.async.bulk, completion on
-// mbarriers).
+// shared memory by bulk asynchronous copies (plan and helpers in rb_stage.cuh).
 //
-// A work item is one band of TB_ROWS rows of one query.  A CTA has mx/4
-// consumer threads (thread t owns the points x0 = 4t .. 4t+3 of every row) and
-// one producer warp.  The item marches over steps k = y0-3 .. y1; stage k brings
-// source row k+1, residual row k and, on the last sweep under Polak-Ribiere,
-// direction row k into ring slot (stage number mod RING).  At step k a consumer
+// Item = band y0 .. y1-1 of one query; steps k = y0-3 .. y1.  Stage k brings
+// source row k+1 and, from k = y0-1 on, residual row k and (last sweep under
+// Polak-Ribiere) direction row k.  At step k a consumer
 //   - shifts its register window of old black source values and adds row k+1
 //     (only the values that the red updates of rows k .. k+2 read),
 //   - updates the red points of row k (red: x + y even) from old black values,
 //   - after the CTA barrier, updates the black points of row k-1 from the new
-//     red values of rows k-2 .. k (registers) and writes row k-1.
-// Neighbours owned by the adjacent threads come from the staged source row
-// (zero-padded at both ends, so x = -1 and x = mx read the Dirichlet zero) or
-// from a small shared array of new red values.  The march is unrolled by two so
-// that the colour pattern of a row is a compile-time constant.
+//     red values of rows k-2 .. k (registers) and the residual row k-1 (stage
+//     k-1), and writes row k-1.
+// Neighbours owned by the adjacent threads come from the staged source row or
+// from a small shared array of new red values.  The march is unrolled by two
+// so that the colour pattern of a row is a compile-time constant.
 //
-// The producer refills the slot of stage k-2 (every read of it ended before the
-// barrier of step k) with stage k-2+RING after that barrier.  Rows outside the
-// grid are copied from a zero row in global memory.  Every mbarrier wait is
-// bounded in time: on expiry the device error flag is raised, the thread stops
-// waiting and marches on whatever the slots hold (the CTA barriers stay
-// matched), then the copies in flight are drained (bounded) and the CTA returns.
+// The last sweep also accumulates r^T y and, under Polak-Ribiere, (A p)^T y
+// with the direction rows k-2 .. k read from their stages (a stage is then read
+// for three steps: LAG 3) and the diagonal rebuilt from the face coefficients,
+// which keeps it near the register budget of the other sweeps.
+//
+// Every mbarrier wait is bounded in time: on expiry the device error flag is
+// raised, the thread stops waiting and marches on whatever the slots hold (the
+// CTA barriers stay matched), then the copies in flight are drained (bounded)
+// and the CTA returns.
 #include "rb_stage.cuh"
 
 namespace rbk {
@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
     __shared__ double red[32];
+    constexpr int LAG = LAST ? 3 : 2;
     const Geo& g = P.g;
     const int mx = g.mx, my = g.my;
     const SmoothLayout<T> lay(mx, LAST);
@@ -64,52 +65,80 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
 
     setup(lay, ring, bar, mx);   // zero pads and edge rows, barriers
 
-    const int nband = (my + TB_ROWS - 1) / TB_ROWS;
     const int cnt = P.lcnt[L_PREC];
+    const int rows = band_rows(my, cnt, P.max_tiles);
+    const int nband = (my + rows - 1) / rows;
     const long long total = (long long)cnt * nband;
-    unsigned seq = 0;   // stages requested so far by this CTA (all threads agree)
+
+    // ---- producer cursor: the next stage in this CTA's order.  Only lane 0 of the
+    // producer warp touches it; it lives in shared memory so that it costs the
+    // consumers no registers.
+    struct Cursor {
+        const T* src;
+        const T* rg;
+        const T* pg;
+        long long w;
+        int y0, y1, k;
+        unsigned issued;
+        bool need_ap;
+    };
+    __shared__ Cursor cur;
+    auto cursor_item = [&](long long w) {
+        cur.w = w;
+        if (w >= total) return;
+        const int slot = (int)(w / nband), band = (int)(w % nband);
+        const int q = P.lidx[L_PREC * P.Bmax + slot];
+        const QState& s = P.st[q];
+        const size_t base = (size_t)q * g.n;
+        cur.src = src_base + base;
+        cur.rg = reinterpret_cast<const T*>(P.r) + base;
+        cur.pg = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
+        cur.y0 = band * rows;
+        cur.y1 = min(my, cur.y0 + rows);
+        cur.k = cur.y0 - 3;
+        cur.need_ap = LAST && P.beta_form == RB_BETA_PR && !s.start;
+    };
+    auto issue_next = [&]() {
+        if (cur.w >= total) return;
+        const unsigned u = cur.issued++;
+        T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
+        uint64_t* b = bar + u % RING;
+        const int kk = cur.k, ms = kk + 1;
+        const bool rp = kk >= cur.y0 - 1;   // residual (and direction) rows from y0-1 on
+        const bool in = kk >= 0 && kk < my;
+        const bool ap = rp && cur.need_ap;
+        mb_arrive_tx(b, row_bytes * (1u + (rp ? 1u : 0u) + (ap ? 1u : 0u)));
+        bulk_row(sg, (ms >= 0 && ms < my) ? cur.src + (size_t)ms * mx : zero_row, row_bytes, b);
+        if (rp) bulk_row(sg + lay.stride, in ? cur.rg + (size_t)kk * mx : zero_row, row_bytes, b);
+        if (ap) bulk_row(sg + 2 * lay.stride, in ? cur.pg + (size_t)kk * mx : zero_row, row_bytes, b);
+        if (++cur.k > cur.y1) cursor_item(cur.w + gridDim.x);
+    };
+    if (issuer) {
+        cur.issued = 0;
+        cursor_item(blockIdx.x);
+        for (int i = 0; i < RING; ++i) issue_next();
+    }
+
+    unsigned seq = 0;   // global step (= stage) number of this CTA (all threads agree)
+    bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / nband), band = (int)(w % nband);
         const int q = P.lidx[L_PREC * P.Bmax + slot];
         const QState& s = P.st[q];
         const bool need_ap = LAST && P.beta_form == RB_BETA_PR && !s.start;
-        const int y0 = band * TB_ROWS, y1 = min(my, y0 + TB_ROWS);
-        const int kfirst = y0 - 3;   // first stage and step (odd)
-        const size_t base = (size_t)q * g.n;
-        const T* src = src_base + base;
-        const T* rg = reinterpret_cast<const T*>(P.r) + base;
-        const T* pg = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * g.n;
-        T* dst = dst_base + base;
-        const uint32_t stage_bytes = row_bytes * (need_ap ? 3u : 2u);
-        __syncthreads();   // the previous item no longer reads the ring, the edges or mus
+        const int y0 = band * rows, y1 = min(my, y0 + rows);
+        const int kfirst = y0 - 3;   // odd
+        T* dst = dst_base + (size_t)q * g.n;
+        __syncthreads();   // the previous item no longer reads mus or the edge rows
         for (int j = threadIdx.x; j < P.n_mu; j += blockDim.x) mus[j] = (T)P.mu[(size_t)q * P.n_mu + j];
+        __syncthreads();
 
-        // stage kk of this item into its slot (producer lane 0)
-        auto issue = [&](int kk) {
-            const unsigned u = seq + (unsigned)(kk - kfirst);
-            T* sg = ring + (size_t)(u % RING) * lay.stage_elems + lay.pad;
-            uint64_t* b = bar + u % RING;
-            mb_arrive_tx(b, stage_bytes);
-            const int ms = kk + 1, mr = kk;
-            bulk_row(sg, (ms >= 0 && ms < my) ? src + (size_t)ms * mx : zero_row, row_bytes, b);
-            bulk_row(sg + lay.stride, (mr >= 0 && mr < my) ? rg + (size_t)mr * mx : zero_row, row_bytes, b);
-            if (need_ap)
-                bulk_row(sg + 2 * lay.stride, (mr >= 0 && mr < my) ? pg + (size_t)mr * mx : zero_row, row_bytes, b);
-        };
-        if (issuer)
-            for (int kk = kfirst; kk <= y1 && kk < kfirst + RING; ++kk) issue(kk);
-        __syncthreads();   // mus visible
-
-        TCoef<T> cf[2];     // coefficients of the last even / odd row updated
+        TCoef<T> cf[2];   // coefficients of the last even / odd row updated
         int key[2] = {-1, -1};
+        int kpf = __ldg(g.rkey + max(y0 - 1, 0));   // key of the next red row, loaded a step ahead
         T sbm[2] = {T(0), T(0)}, sbc[2] = {T(0), T(0)}, sbp[2] = {T(0), T(0)};   // old black source values
-        T rr[2][4];               // residual rows of even / odd parity
         T zm[2] = {T(0), T(0)}, zc[2] = {T(0), T(0)}, zp[2] = {T(0), T(0)};      // new red rows k-2, k-1, k
-        T pm[4], pc[4], pn[4];    // direction rows k-2, k-1, k
-#pragma unroll
-        for (int j = 0; j < 4; ++j) rr[0][j] = rr[1][j] = pm[j] = pc[j] = pn[j] = T(0);
         T ry = T(0), apy = T(0);
-        bool ok = true;
         unsigned cslot = seq % RING, cpar = (seq / RING) & 1u;
 
         // one step of the march; PAR = k & 1
@@ -118,8 +147,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
             constexpr int R0 = PAR, R1 = PAR + 2;   // red columns of row k = black columns of row k-1
             if (!producer) {
                 const T* stg = ring + (size_t)cslot * lay.stage_elems + lay.pad;
-                const unsigned pslot = cslot == 0 ? RING - 1 : cslot - 1;
-                const T* prev = ring + (size_t)pslot * lay.stage_elems + lay.pad;   // stage k-1
+                const T* prev = ring + (size_t)(cslot == 0 ? RING - 1 : cslot - 1) * lay.stage_elems + lay.pad;
                 if (ok && !mb_wait(bar + cslot, cpar, P.err)) ok = false;
                 // source row k+1 at the red columns of row k (its black points)
                 const V4t<T> sn = lds4(stg + x0);
@@ -130,31 +158,20 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
                 sbp[0] = sn.v[R0];
                 sbp[1] = sn.v[R1];
                 if (k >= y0 - 1) {
-                    const V4t<T> rk = lds4(stg + lay.stride + x0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) rr[PAR][j] = rk.v[j];
-                    if (need_ap) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            pm[j] = pc[j];
-                            pc[j] = pn[j];
-                        }
-                        const V4t<T> pv = lds4(stg + 2 * lay.stride + x0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) pn[j] = pv.v[j];
-                    }
                     // red half-sweep of row k
                     zm[0] = zc[0];
                     zm[1] = zc[1];
                     zc[0] = zp[0];
                     zc[1] = zp[1];
                     if (k >= 0 && k < my) {
-                        const int kk = tkey(g, k);
+                        const int kk = kpf;
+                        kpf = __ldg(g.rkey + min(k + 1, my - 1));
                         if (kk != key[PAR]) {
                             tcoef<T>(g, mus, x0, k, cf[PAR]);
                             key[PAR] = kk;
                         }
                         const TCoef<T>& c = cf[PAR];
+                        const V4t<T> rk = lds4(stg + lay.stride + x0);
                         // source row k (previous stage): the horizontal neighbour across the thread edge
                         const T halo = PAR == 0 ? prev[x0 - 1] : prev[x0 + 4];
                         // PAR 0: red 0 (halo, sbc0), red 2 (sbc0, sbc1); PAR 1: red 1 (sbc0, sbc1), red 3 (sbc1, halo)
@@ -178,16 +195,16 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
                     const int b = k - 1;
                     if (b >= y0 && b < y1) {
                         const TCoef<T>& c = cf[1 - PAR];
-                        const T* rb = rr[1 - PAR];
+                        const V4t<T> rb = lds4(prev + lay.stride + x0);   // residual row b
                         const T* ze = zedge + (b & 3) * lay.zstride;
                         // PAR 0 (b odd): black 0 (t-1's red 3, zc0), black 2 (zc0, zc1)
                         // PAR 1 (b even): black 1 (zc0, zc1), black 3 (zc1, t+1's red 0)
                         const T zh = PAR == 0 ? ze[t] : ze[t + 2];
                         const T l0 = PAR == 0 ? zh : zc[0], r0 = PAR == 0 ? zc[0] : zc[1];
                         const T l1 = PAR == 0 ? zc[0] : zc[1], r1 = PAR == 0 ? zc[1] : zh;
-                        const T n0 = rb[R0] + c.kx[R0] * l0 + c.kx[R0 + 1] * r0 + c.kym[R0] * zm[0] +
+                        const T n0 = rb.v[R0] + c.kx[R0] * l0 + c.kx[R0 + 1] * r0 + c.kym[R0] * zm[0] +
                                      c.kyp[R0] * zp[0];
-                        const T n1 = rb[R1] + c.kx[R1] * l1 + c.kx[R1 + 1] * r1 + c.kym[R1] * zm[1] +
+                        const T n1 = rb.v[R1] + c.kx[R1] * l1 + c.kx[R1 + 1] * r1 + c.kym[R1] * zm[1] +
                                      c.kyp[R1] * zp[1];
                         V4t<T> out;
                         out.v[R0] = n0 * c.idiag[R0];
@@ -197,17 +214,23 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
                         stg4(dst + (size_t)b * mx + x0, out);
                         if constexpr (LAST) {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) ry += rb[j] * out.v[j];
+                            for (int j = 0; j < 4; ++j) ry += rb.v[j] * out.v[j];
                             if (need_ap) {
-                                // direction row b (previous stage): neighbours across the thread edges
-                                const T* pb = prev + 2 * lay.stride;
-                                const T pl = pb[x0 - 1], pr = pb[x0 + 4];
+                                // direction rows b-1, b, b+1 from stages k-2, k-1, k
+                                const T* prev2 =
+                                    ring + (size_t)(cslot >= 2 ? cslot - 2 : cslot + RING - 2) * lay.stage_elems +
+                                    lay.pad;
+                                const V4t<T> pm = lds4(prev2 + 2 * lay.stride + x0);
+                                const V4t<T> pc = lds4(prev + 2 * lay.stride + x0);
+                                const V4t<T> pn = lds4(stg + 2 * lay.stride + x0);
+                                const T pl = prev[2 * lay.stride + x0 - 1], pr = prev[2 * lay.stride + x0 + 4];
 #pragma unroll
                                 for (int j = 0; j < 4; ++j) {
-                                    const T xl = j == 0 ? pl : pc[j - 1];
-                                    const T xr = j == 3 ? pr : pc[j + 1];
-                                    const T ap = c.diag[j] * pc[j] - (c.kx[j] * xl + c.kx[j + 1] * xr +
-                                                                      c.kym[j] * pm[j] + c.kyp[j] * pn[j]);
+                                    const T xl = j == 0 ? pl : pc.v[j - 1];
+                                    const T xr = j == 3 ? pr : pc.v[j + 1];
+                                    const T dg = c.kx[j] + c.kx[j + 1] + c.kym[j] + c.kyp[j];
+                                    const T ap = dg * pc.v[j] - (c.kx[j] * xl + c.kx[j + 1] * xr + c.kym[j] * pm.v[j] +
+                                                                 c.kyp[j] * pn.v[j]);
                                     apy += ap * out.v[j];
                                 }
                             }
@@ -218,9 +241,9 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
                 }
             } else {
                 __syncthreads();
-                // refill: stage k-2 is no longer read
-                if (issuer && k - 2 >= kfirst && k - 2 + RING <= y1) issue(k - 2 + RING);
+                if (issuer && seq >= (unsigned)LAG) issue_next();   // stage seq-LAG is no longer read
             }
+            ++seq;
             if (++cslot == RING) {
                 cslot = 0;
                 cpar ^= 1u;
@@ -230,10 +253,9 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_tma(Params P, const
             step(Par1{}, k);
             if (k + 1 <= y1) step(Par0{}, k + 1);
         }
-        seq += (unsigned)(y1 - kfirst + 1);
         // an expired wait anywhere in the CTA: let the requested copies land (bounded), then stop
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, seq);
+            if (issuer) drain(bar, cur.issued);
             __syncthreads();
             return;
         }

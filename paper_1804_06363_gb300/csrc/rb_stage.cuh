@@ -3,13 +3,17 @@
 // copies (cp.async.bulk) that complete on mbarriers, issued by one producer
 // lane; every wait on a copy is bounded in time.
 //
-// Common plan of a staged kernel.  A work item is one band of TB_ROWS rows of
-// one query.  The CTA has mx/4 consumer threads (thread t owns the points
-// x0 = 4t .. 4t+3 of every row) and one producer warp.  The item marches over
-// steps k; stage k (the rows that step k consumes) lands in ring slot
-// (stage number mod RING).  Every thread passes one CTA barrier per step; the
-// producer refills the slot of stage k-2 after the barrier of step k, so a
-// stage may be read during its own step and the next one.  Staged rows are
+// Common plan of a staged kernel.  A work item is one band of rows of one query
+// (TB_ROWS rows, fewer when the work list is short: band_rows).  The CTA has
+// mx/4 consumer threads (thread t owns the points x0 = 4t .. 4t+3 of every row)
+// and one producer warp, and walks its items (grid-stride order) as one
+// continuous march: the item's steps k each consume one stage (the rows that
+// step needs), stages are numbered across items, and stage u lands in ring
+// slot u mod RING.  Every thread passes one CTA barrier per step.  A stage is
+// read in its own step and at most LAG-1 following ones, so after the barrier
+// of global step g the producer refills the slot of stage g-LAG with the next
+// stage of its cursor, which runs ahead into the next item: the copies of a
+// new band are in flight before the previous band ends.  Staged rows are
 // padded with 16 bytes of zeros on both sides (x = -1 and x = mx read the
 // Dirichlet zero); rows outside the grid are copied from a zero row.
 #pragma once
@@ -181,6 +185,7 @@ struct Layout {
 };
 
 // zero the pads of every staged row and `extra` elements after the ring; init the barriers
+// (ends with a CTA barrier)
 template <typename T>
 __device__ __forceinline__ void setup(const Layout<T>& lay, T* ring, uint64_t* bar, int mx) {
     for (int i = threadIdx.x; i < RING * lay.arrays; i += blockDim.x) {
@@ -197,6 +202,17 @@ __device__ __forceinline__ void setup(const Layout<T>& lay, T* ring, uint64_t* b
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    __syncthreads();   // barriers initialised and pads zeroed before the first copy is issued
+}
+
+// Rows per band: TB_ROWS, halved (down to 16) while the work items (queries x
+// bands) would leave part of the grid idle, and never more bands than a query
+// has partial-sum slots.  Uniform across the grid; always even.
+__device__ __forceinline__ int band_rows(int my, int cnt, int max_tiles) {
+    int rows = TB_ROWS;
+    while (rows > 16 && (long long)cnt * ((my + rows - 1) / rows) < (long long)gridDim.x) rows >>= 1;
+    while ((my + rows - 1) / rows > max_tiles) rows <<= 1;
+    return rows;
 }
 
 // CTA sum of per-thread partials (FP64 across warps); result in thread 0
