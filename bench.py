@@ -27,8 +27,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
 
 # DRAM bytes per grid point and query measured by ncu for the dominant kernel (small case,
 # profiles/rbcg_2d_512_smoother_dram.md); scaled to a full launch by its units.
-NCU_TRAFFIC = {("f32", "smooth"): {"intermediate": 11.4, "last": 17.0,
-                                   "source": "profiles/rbcg_2d_512_smoother_dram.md"}}
+NCU_TRAFFIC = {}
 
 # Algorithmic bytes per grid point per launch unit (one query, one pass), by kernel
 # and inner precision: every operand read or written once (eq. 5-8 and Alg. 3 steps).
@@ -37,6 +36,10 @@ BYTES_PER_POINT = {
             "outer_residual": 12, "outer_update": 24},
     "f64": {"cg_a": 24, "cg_b": 40, "smooth": 32, "project": 8, "prolong": 8, "outer_residual": 16},
 }
+# With BF16 storage of the preconditioner's intermediate vectors: the prolongation writes
+# 2 B; a sweep before the last reads source (2) and r (4) and writes 2; the last reads
+# source (2), r (4), p (4) and writes y (4).
+BF16_SMOOTH_LAST, BF16_SMOOTH_SWEEP, BF16_PROLONG = 14, 8, 2
 
 
 def parse():
@@ -52,7 +55,8 @@ def parse():
     ap.add_argument("--gemm", default="auto")
     ap.add_argument("--fp64-queries", type=int, default=256, help="queries of the FP64 plain comparator (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=40, help="Alg. 3 iterations per core in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=300,
+                    help="Alg. 3 iterations per core in the CPU sample (about 10 s of oracle work)")
     ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --nu, --gemm as given)")
     ap.add_argument("--quick", action="store_true",
@@ -221,7 +225,8 @@ def main():
     if not args.no_tune:
         tB = min(B, 256)
         tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
-        opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"])
+        opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
+                    store=tuned["store"])
         tuned["sample"] = f"{tB} training parameters"
 
     def step(xbuf, **kw):
@@ -278,21 +283,29 @@ def main():
              "outer_update": outers}
     kernels = {}
     es = 4 if prec == "f32" else 8
+    bf16 = prec == "f32" and opts.get("store", "f32") == "bf16"
     for k, (n_launch, ms) in prof.items():
         bpp = BYTES_PER_POINT[prec].get(k)
+        if bf16 and k in ("prolong", "tc_prolong"):
+            bpp = BF16_PROLONG
         entry = {"launches": n_launch, "ms": round(ms, 3)}
         if bpp is not None and ms > 0:
             alg = bpp * N * units[k]
             if k == "smooth":   # nu sweeps: the last one also reads the direction p (PR term)
-                alg = (bpp + 3 * es * (max(1, opts["nu"]) - 1)) * N * iters
+                if bf16:
+                    bpp = BF16_SMOOTH_LAST
+                    alg = (BF16_SMOOTH_LAST + BF16_SMOOTH_SWEEP * (max(1, opts["nu"]) - 1)) * N * iters
+                else:
+                    alg = (bpp + 3 * es * (max(1, opts["nu"]) - 1)) * N * iters
             entry["alg_bytes"] = alg
+            entry["alg_bytes_per_point"] = round(alg / (N * max(1, units[k] if k != "smooth" else iters)), 2)
             entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
         kernels[k] = entry
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     peak, peak_kind = measured_peaks()
     achieved = kernels[dom].get("gbs")
     traffic = None
-    nt = NCU_TRAFFIC.get((prec, dom))
+    nt = NCU_TRAFFIC.get((prec, opts.get("store", "f32"), dom))
     if nt is not None and dom == "smooth" and kernels[dom]["launches"]:
         # one "smooth" launch = nu sweeps; bytes scaled to the average launch of this run
         per_launch_units = iters / kernels[dom]["launches"]
@@ -302,8 +315,9 @@ def main():
                 "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
                 "traffic_source": nt["source"] if nt else None,
                 "peak_source": peak_kind,
-                "alg_bytes_per_unit": BYTES_PER_POINT[prec].get(dom), "alg_bytes_per_launch": round(alg_per_launch),
-                "unit_def": "one query x one grid point per launch"}
+                "alg_bytes_per_unit": kernels[dom].get("alg_bytes_per_point"),
+                "alg_bytes_per_launch": round(alg_per_launch),
+                "unit_def": "one query x one grid point x one launch (smooth: the nu sweeps of one preconditioner application)"}
 
     # ---- end to end through the C interface with host buffers (pinned)
     xh = torch.zeros((B, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -369,6 +383,7 @@ def main():
             "config": {"workload": w.name, "grid": "x".join(map(str, prob.dims)), "P": prob.P, "n_basis": w.n_basis,
                        "queries_per_step_per_gpu": B, "precision": args.precision, "beta": "pr",
                        "smoother": f"red-black GS nu={opts['nu']}", "tol": 1e-10, "gemm": opts["gemm"],
+                       "kernels": opts.get("kernels", 0), "store": opts.get("store", "f32"),
                        "inner_tol": opts.get("inner_tol"), "autotuned": tuned,
                        "l2": "inputs larger than L2 (FP64 solutions %.1f GB + FP32 work vectors per step)"
                              % (B * N * 8 / 1e9),

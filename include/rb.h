@@ -68,6 +68,7 @@ enum { RB_PREC_FP64 = 0, RB_PREC_MIXED = 1 };
 enum { RB_BETA_FR = 0, RB_BETA_PR = 1 };
 enum { RB_X0_ZERO = 0, RB_X0_GIVEN = 1 };
 enum { RB_GEMM_AUTO = 0, RB_GEMM_CUDA_CORES = 1, RB_GEMM_TENSOR = 2 };
+enum { RB_STORE_F32 = 0, RB_STORE_BF16 = 1 };
 
 typedef struct {
     double tol;         /* stop at ||f - A x|| / ||f|| < tol (true FP64 residual) */
@@ -90,6 +91,12 @@ typedef struct {
                            1: as 0, but all red-black sweeps fused in one pass (FP32 mixed path,
                               nu <= 6);
                            2: CG body and one smoother pass per sweep with rows held in registers */
+    int store;          /* RB_STORE_*: storage of the preconditioner's intermediate vectors (the
+                           prolongation W e_N and the smoother sweeps before the last one).
+                           RB_STORE_BF16 halves their bytes; the arithmetic stays FP32 and the
+                           preconditioned residual y is FP32.  It applies to the mixed solver with
+                           the red-black smoother and kernels = 0 on 2D grids whose rows hold a
+                           multiple of 128 points; elsewhere the storage is FP32. */
     void* stream;       /* cudaStream_t or NULL */
 } rb_opts;
 
@@ -109,7 +116,8 @@ typedef struct {
 } rb_build_opts;
 
 /* Fill defaults: tol 1e-10, red-black Gauss-Seidel with nu = 1, FP64, PR beta,
- * zero start, inner_tol 1e-5, max_outer 12, automatic GEMM engine, graphs on. */
+ * zero start, inner_tol 1e-5, max_outer 12, automatic GEMM engine, graphs on,
+ * staged kernels (kernels = 0), FP32 storage. */
 void rb_default_opts(rb_opts* opts);
 void rb_default_build_opts(rb_build_opts* opts);
 
@@ -196,8 +204,10 @@ rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double
 /* Autotuner.  Times rb_pcg on the B sample queries (host mu; x host or device
  * [B][N_dof] scratch) and picks, by coordinate descent from *opts, the smoother
  * sweep count nu (1..6; the paper leaves the smoother's iteration count open,
- * Section 3.1), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6; mixed only),
- * the smoother kernels (rb_opts.kernels) and the GEMM engine (mixed only).  Only configurations under which every
+ * Section 3.1) for each storage of the preconditioner's intermediate vectors that
+ * applies (rb_opts.store), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6;
+ * mixed only), the smoother kernels (rb_opts.kernels) and the GEMM engine (mixed
+ * only).  Only configurations under which every
  * sample query converges are eligible.  Writes the fastest into *opts and
  * summarises it in *res (may be NULL). */
 typedef struct {
@@ -206,6 +216,8 @@ typedef struct {
     int gemm;
     double ms_per_solve;   /* of the chosen configuration on the sample */
     int trials;
+    int kernels;
+    int store;
 } rb_tune_result;
 rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* opts, rb_tune_result* res);
 

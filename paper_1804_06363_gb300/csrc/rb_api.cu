@@ -429,6 +429,11 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bo
     P.smoother = o.smoother;
     P.omega = o.omega;
     P.mixed = m.mixed ? 1 : 0;
+    // BF16 iterates only where the staged red-black smoother runs (the mixed path)
+    P.ybf16 = (m.mixed && o.store == RB_STORE_BF16 && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 &&
+               !ctx->force_generic && use_rowmarch(ctx->geo) && use_tma_smoother(ctx->geo))
+                  ? 1
+                  : 0;
     return P;
 }
 
@@ -572,7 +577,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
-        (o.kernels < 0 || o.kernels > 2) ||
+        (o.kernels < 0 || o.kernels > 2) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
         (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED)) {
         ctx->err = "invalid options";
         return RB_EINVAL;
@@ -769,6 +774,7 @@ void rb_default_opts(rb_opts* o) {
     o->gemm = RB_GEMM_AUTO;
     o->graph = 1;
     o->kernels = 0;
+    o->store = RB_STORE_F32;
     o->stream = nullptr;
 }
 
@@ -996,12 +1002,21 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
     };
     rb_opts best = *opts;
     double best_ms = trial(best);
-    for (int nu = 1; nu <= 6; ++nu) {
-        if (nu == best.nu) continue;
-        rb_opts t = best;
-        t.nu = nu;
-        const double ms = trial(t);
-        if (ms < best_ms) { best_ms = ms; best = t; }
+    // sweep count, for each storage of the smoother's iterates that applies (BF16
+    // makes a sweep cheaper and may move the best nu)
+    const bool bf16_ok = opts->precision == RB_PREC_MIXED && opts->smoother == RB_SMOOTH_RBGS &&
+                         !ctx->force_generic && use_rowmarch(ctx->geo) && use_tma_smoother(ctx->geo);
+    const rb_opts start = best;
+    for (int store = RB_STORE_F32; store <= (bf16_ok ? RB_STORE_BF16 : RB_STORE_F32); ++store) {
+        for (int nu = 1; nu <= 6; ++nu) {
+            if (nu == start.nu && store == start.store) continue;
+            rb_opts t = start;
+            t.nu = nu;
+            t.store = store;
+            if (store == RB_STORE_BF16) t.kernels = 0;
+            const double ms = trial(t);
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
     }
     if (best.precision == RB_PREC_MIXED) {
         const double tols[3] = {1e-4, 1e-5, 1e-6};
@@ -1023,6 +1038,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             const rb_opts base = best;
             for (int kk = 0; kk <= 2; ++kk) {
                 if (kk == base.kernels || (kk == 1 && !use_fused_smoother(ctx->geo, base.nu))) continue;
+                if (kk != 0 && base.store == RB_STORE_BF16) continue;   // BF16 iterates need kernels = 0
                 rb_opts t = base;
                 t.kernels = kk;
                 const double ms = trial(t);
@@ -1040,6 +1056,8 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
         res->gemm = best.gemm;
         res->ms_per_solve = best_ms / B;
         res->trials = trials;
+        res->kernels = best.kernels;
+        res->store = best.store;
     }
     return RB_OK;
 }

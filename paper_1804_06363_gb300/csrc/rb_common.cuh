@@ -108,6 +108,7 @@ struct Params {
     int beta_form, smoother;
     double omega;
     int mixed;                   // 1: T = float inner with FP64 refinement
+    int ybf16;                   // 1: the smoother's iterates (ypro, tmp) are stored as BF16
 };
 
 // ----------------------------------------------------------------------------

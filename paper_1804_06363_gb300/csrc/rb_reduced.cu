@@ -2,6 +2,8 @@
 // (eq. 6) with the Cholesky factor of A_N(mu) (eq. 12b), prolongation W e_N
 // (eq. 7), plus the offline-build helpers (Gram-Schmidt, greedy scores).
 // CUDA-core versions, used for FP64 and as the reference engine of the mixed path.
+#include <cuda_bf16.h>
+
 #include "rb_common.cuh"
 
 namespace rbk {
@@ -164,7 +166,10 @@ __global__ void __launch_bounds__(THREADS) k_prolong(Params P) {
                 if (q < 0) continue;
                 T v = acc[gq];
                 if constexpr (ADDX) v += (T)P.x64[(size_t)q * n + i];
-                reinterpret_cast<T*>(P.ypro)[(size_t)q * n + i] = v;
+                if (sizeof(T) == 4 && P.ybf16)
+                    reinterpret_cast<__nv_bfloat16*>(P.ypro)[(size_t)q * n + i] = __float2bfloat16_rn((float)v);
+                else
+                    reinterpret_cast<T*>(P.ypro)[(size_t)q * n + i] = v;
             }
         }
     }

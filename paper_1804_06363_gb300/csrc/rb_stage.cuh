@@ -46,8 +46,11 @@ __device__ __forceinline__ uint64_t gtime() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ void mb_init(uint64_t* b) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s2u(b)) : "memory");
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t count = 1) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s2u(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s2u(b)) : "memory");
 }
 __device__ __forceinline__ void mb_arrive_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s2u(b)), "r"(bytes) : "memory");
@@ -213,6 +216,70 @@ __device__ __forceinline__ int band_rows(int my, int cnt, int max_tiles) {
     while (rows > 16 && (long long)cnt * ((my + rows - 1) / rows) < (long long)gridDim.x) rows >>= 1;
     while ((my + rows - 1) / rows > max_tiles) rows <<= 1;
     return rows;
+}
+
+// ---- warp-specialised kernels: the consumer threads are the first nthr threads
+// (a multiple of 32) and synchronise among themselves on named barrier 1; the
+// producer warp never takes part after set-up.
+
+__device__ __forceinline__ void cbar(int nthr) { asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); }
+
+// consumer sum of two per-thread partials (FP64 across warps); result in thread 0
+template <typename T>
+__device__ __forceinline__ void csum2(T a, T b, double* red, double out[2], int nthr) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    cbar(nthr);   // red[] free
+    if (lane == 0) {
+        red[wi] = (double)a;
+        red[16 + wi] = (double)b;
+    }
+    cbar(nthr);
+    out[0] = out[1] = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nthr / 32; ++i) {
+            out[0] += red[i];
+            out[1] += red[16 + i];
+        }
+}
+
+// Thread 0 publishes the consumer partials of (q, tile); true in every consumer
+// thread of the CTA that arrives last for q (then all partials of q are visible).
+__device__ __forceinline__ bool carrive(const Params& P, int q, int tile, int ntiles, const double* vals, int nv,
+                                        int nthr, int* s_flag) {
+    if (threadIdx.x == 0) {
+        double* dst = P.part + ((size_t)q * P.max_tiles + tile) * 4;
+        for (int j = 0; j < nv; ++j) dst[j] = vals[j];
+        __threadfence();
+        const unsigned prev = atomicAdd(P.tick + q, 1u);
+        *s_flag = (prev == (unsigned)ntiles - 1u);
+    }
+    cbar(nthr);
+    const bool last = *s_flag != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// fixed-order consumer sum of the nv partials of q over its tiles; result in thread 0
+__device__ __forceinline__ void cgather(const Params& P, int q, int ntiles, int nv, double* out, double* red,
+                                        int nthr) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    for (int j = 0; j < nv; ++j) {
+        double s = 0.0;
+        for (int t = threadIdx.x; t < ntiles; t += nthr) s += __ldcg(P.part + ((size_t)q * P.max_tiles + t) * 4 + j);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        cbar(nthr);
+        if (lane == 0) red[wi] = s;
+        cbar(nthr);
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int i = 0; i < nthr / 32; ++i) tot += red[i];
+            out[j] = tot;
+        }
+    }
 }
 
 // CTA sum of per-thread partials (FP64 across warps); result in thread 0

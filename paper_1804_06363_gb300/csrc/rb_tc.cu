@@ -18,6 +18,8 @@
 // the other roles stop, in-flight copies are drained (bounded) and TMEM freed.
 #include "rb_tc.cuh"
 
+#include <cuda_bf16.h>
+
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -362,6 +364,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quad = warp & 3;
         const int prow = quad * 32 + lane;          // point within the tile (TMEM lane)
         float* ybase = reinterpret_cast<float*>(P.ypro) + (size_t)q0 * n;
+        __nv_bfloat16* hbase = reinterpret_cast<__nv_bfloat16*>(P.ypro) + (size_t)q0 * n;   // BF16 storage
+        const bool bf = P.ybf16 != 0;
         for (int i = 0; i < np; ++i) {
             const int ab = i & 1;
             bool ok = mbar_wait(tfull + ab, (i >> 1) & 1, err);
@@ -374,9 +378,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 float v[16];
                 tmem_ld16(tmem + (uint32_t)(ab * 128) + ((uint32_t)(quad * 32) << 16) + (uint32_t)cc, v);
                 if (inside) {
+                    if (bf) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (s_act[cc + j]) __stcs(ybase + (size_t)(cc + j) * n + pt, v[j]);
+                        for (int j = 0; j < 16; ++j)
+                            if (s_act[cc + j])
+                                __stcs(reinterpret_cast<unsigned short*>(hbase + (size_t)(cc + j) * n + pt),
+                                       __bfloat16_as_ushort(__float2bfloat16_rn(v[j])));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (s_act[cc + j]) __stcs(ybase + (size_t)(cc + j) * n + pt, v[j]);
+                    }
                 }
             }
             tc_fence_before();

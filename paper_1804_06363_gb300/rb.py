@@ -22,6 +22,7 @@ SMOOTHERS = {"none": 0, "rbgs": 1, "jacobi": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 BETAS = {"fr": 0, "pr": 1}
 GEMMS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
+STORES = {"f32": 0, "bf16": 1}
 
 
 class RbLoad(C.Structure):
@@ -37,7 +38,7 @@ class RbOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("smoother", C.c_int), ("nu", C.c_int),
                 ("omega", C.c_double), ("precision", C.c_int), ("beta_form", C.c_int), ("x0_mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("gemm", C.c_int), ("graph", C.c_int),
-                ("kernels", C.c_int), ("stream", C.c_void_p)]
+                ("kernels", C.c_int), ("store", C.c_int), ("stream", C.c_void_p)]
 
 
 class RbStats(C.Structure):
@@ -52,7 +53,7 @@ class RbBuildOpts(C.Structure):
 
 class RbTuneResult(C.Structure):
     _fields_ = [("nu", C.c_int), ("inner_tol", C.c_double), ("gemm", C.c_int), ("ms_per_solve", C.c_double),
-                ("trials", C.c_int)]
+                ("trials", C.c_int), ("kernels", C.c_int), ("store", C.c_int)]
 
 
 class RbKernelTime(C.Structure):
@@ -170,6 +171,8 @@ def make_opts(**kw) -> RbOpts:
             k, v = "beta_form", BETAS[v] if isinstance(v, str) else v
         elif k == "gemm":
             v = GEMMS[v] if isinstance(v, str) else v
+        elif k == "store":
+            v = STORES[v] if isinstance(v, str) else v
         elif k == "x0":
             k, v = "x0_mode", 1 if v else 0
         elif k == "stream":
@@ -320,7 +323,8 @@ class Context:
         self._check(lib().rb_autotune(self._h, mu.shape[0], _ptr(mu), _ptr(x), C.byref(o), C.byref(r)))
         inv = {v: k for k, v in GEMMS.items()}
         return {"nu": r.nu, "inner_tol": r.inner_tol, "gemm": inv.get(r.gemm, r.gemm),
-                "ms_per_solve": r.ms_per_solve, "trials": r.trials}
+                "ms_per_solve": r.ms_per_solve, "trials": r.trials, "kernels": r.kernels,
+                "store": {v: k for k, v in STORES.items()}.get(r.store, r.store)}
 
     def profile(self, enable: bool) -> None:
         """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""

@@ -274,6 +274,45 @@ def test_staged_smoother_matches_register_kernels_and_oracle(dims, blocks, nu, B
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,blocks,nu", [((128, 300), (3, 3), 3), ((256, 96), (2, 3), 1)])
+def test_bf16_storage_of_preconditioner_vectors(dims, blocks, nu):
+    """BF16 storage of W e_N and of the sweeps before the last (arithmetic FP32):
+    y stays within the rounding of the nu stored vectors (8 significant bits each,
+    relative 2^-9, not amplified by the Gauss-Seidel sweeps) of the FP32-storage y,
+    and the mixed solver still reaches the truth solution (the FP64 refinement
+    decides the accuracy)."""
+    w = wl.small(dims, blocks, n_basis=6, n_train=24, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    r = np.random.default_rng(4).standard_normal((3, prob.n_dof)).astype(np.float32)
+    for gemm in ("cuda_cores", "auto"):
+        y32 = ctx.precondition(mu, r, precision="mixed", nu=nu, gemm=gemm, store="f32")
+        y16 = ctx.precondition(mu, r, precision="mixed", nu=nu, gemm=gemm, store="bf16")
+        assert not np.array_equal(y16, y32), "BF16 storage not taken"
+        scale = np.abs(y32).max()
+        assert np.abs(y16 - y32).max() <= 4 * nu * 2.0 ** -9 * scale, gemm
+        assert np.abs(y16 - y32).mean() <= nu * 2.0 ** -9 * scale, gemm
+        x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+        status, st = ctx.pcg(mu, x, precision="mixed", nu=nu, gemm=gemm, store="bf16")
+        assert status == rb.RB_OK
+        for b in range(3):
+            assert st["rel_res"][b] < 1e-10
+            assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9
+    ctx.close()
+    # grids outside the staged smoother keep FP32 storage: bit-identical results
+    w = wl.small((62, 70), (2, 3), n_basis=6, n_train=24, bumps=True)
+    basis = greedy.greedy(w.problem, w.train_mu(), w.n_basis)
+    ctx = rb.Context.from_arrays(w.problem, basis.W, basis.ANq, basis.fNr, max_batch=2)
+    r = np.random.default_rng(5).standard_normal((2, w.problem.n_dof)).astype(np.float32)
+    mu = w.test_mu(2)
+    a = ctx.precondition(mu, r, precision="mixed", nu=2, store="f32")
+    b = ctx.precondition(mu, r, precision="mixed", nu=2, store="bf16")
+    np.testing.assert_array_equal(a, b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("dims,blocks,nu", [((40, 36), (3, 3), 1), ((128, 40), (3, 2), 3), ((14, 12, 10), (2, 2, 2), 2)])
 def test_preconditioner_matches_oracle(dims, blocks, nu):
     """y = RBI(A(mu), r, W, 1) (eqs. 5-8) against the oracle's: FP64 to round-off, the mixed
