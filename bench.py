@@ -25,9 +25,10 @@ sys.path.insert(0, ROOT)
 METRIC = "RB-PCG solves/sec to rel. residual 1e-10 (mixed+batched vs FP64 plain), % HBM roofline"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
 
-# DRAM bytes per grid point and query measured by ncu for the dominant kernel (small case,
-# profiles/rbcg_2d_512_smoother_dram.md); scaled to a full launch by its units.
-NCU_TRAFFIC = {}
+# DRAM bytes per grid point and query measured by ncu for the dominant kernel (256-query case,
+# profiles/rbcg_2d_512_smoother_staged.md); scaled to a full launch by its units.
+NCU_TRAFFIC = {("f32", "f32", "smooth"): {"intermediate": 11.57, "last": 15.86,
+                                          "source": "profiles/rbcg_2d_512_smoother_staged.md"}}
 
 # Algorithmic bytes per grid point per launch unit (one query, one pass), by kernel
 # and inner precision: every operand read or written once (eq. 5-8 and Alg. 3 steps).

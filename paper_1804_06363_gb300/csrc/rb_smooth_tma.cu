@@ -47,17 +47,16 @@ template <typename T, typename S>
 struct SmoothLayout {
     int nthr, zstride, arrays_t;
     size_t s_stride, t_stride, stage, zedge_off, bar_off, bytes;
-    __host__ __device__ SmoothLayout(int mx, bool last) {
-        nthr = mx / 4;
-        zstride = (nthr + 2 + 3) & ~3;
-        arrays_t = last ? 2 : 1;
-        s_stride = (size_t)mx * sizeof(S) + 32;
-        t_stride = (size_t)mx * sizeof(T) + 32;
-        stage = s_stride + (size_t)arrays_t * t_stride;
-        zedge_off = (size_t)RING * stage;
-        bar_off = zedge_off + (size_t)4 * zstride * sizeof(T);
-        bytes = bar_off + (size_t)2 * RING * sizeof(uint64_t);   // full[RING], empty[RING]
-    }
+    __host__ __device__ constexpr SmoothLayout(int mx, bool last)
+        : nthr(mx / 4),
+          zstride((mx / 4 + 2 + 3) & ~3),
+          arrays_t(last ? 2 : 1),
+          s_stride((size_t)mx * sizeof(S) + 32),
+          t_stride((size_t)mx * sizeof(T) + 32),
+          stage(s_stride + (size_t)arrays_t * t_stride),
+          zedge_off((size_t)RING * stage),
+          bar_off(zedge_off + (size_t)4 * zstride * sizeof(T)),
+          bytes(bar_off + (size_t)2 * RING * sizeof(uint64_t)) {}   // full[RING], empty[RING]
 };
 
 // loads of 4 consecutive staged values as T, and their stores
@@ -130,8 +129,10 @@ __device__ __noinline__ void smooth_producer(const Params& P, const S* __restric
     drain(full, u);   // copies still in flight (only after an expired wait do any remain)
 }
 
-// S: storage of the source rows (and of dst unless LAST); dst of the last sweep is T
-template <typename T, bool LAST, typename S>
+// S: storage of the source rows (and of dst unless LAST); dst of the last sweep is T.
+// MX: the row length as a compile-time constant (all shared-memory offsets become
+// immediates), or 0 for the runtime P.g.mx.
+template <typename T, bool LAST, typename S, int MX>
 __global__ void __maxnreg__(sizeof(T) == 4 ? 96 : 168) k2_smooth_tma(Params P, const S* __restrict__ src_base,
                                                                     std::conditional_t<LAST, T, S>* dst_base) {
     using D = std::conditional_t<LAST, T, S>;
@@ -141,7 +142,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 96 : 168) k2_smooth_tma(Params P, c
     __shared__ int s_flag;
     constexpr int LAG = LAST ? 3 : 2;
     const Geo& g = P.g;
-    const int mx = g.mx, my = g.my;
+    const int mx = MX > 0 ? MX : g.mx, my = g.my;
     const SmoothLayout<T, S> lay(mx, LAST);
     unsigned char* ring = smem_raw;
     T* zedge = reinterpret_cast<T*>(smem_raw + lay.zedge_off);   // zeroed once; then by byte offset
@@ -364,18 +365,24 @@ bool use_tma_smoother(const Geo& g) {
            tma_smem<double, double>(g, true) <= 200u * 1024u;
 }
 
-template <typename T, bool LAST, typename S>
-static void launch_tma_one(const Params& P, const Launch& L, const S* src, std::conditional_t<LAST, T, S>* dst) {
+template <typename T, bool LAST, typename S, int MX>
+static void launch_tma_mx(const Params& P, const Launch& L, const S* src, std::conditional_t<LAST, T, S>* dst) {
     const size_t smem = tma_smem<T, S>(P.g, LAST);
     const int threads = P.g.mx / 4 + 32;
     static size_t conf_smem = 0;
     static int conf_threads = 0, grid = 0;
     if (conf_smem != smem || conf_threads != threads) {
-        grid = resident(k2_smooth_tma<T, LAST, S>, threads, smem);
+        grid = resident(k2_smooth_tma<T, LAST, S, MX>, threads, smem);
         conf_smem = smem;
         conf_threads = threads;
     }
-    k2_smooth_tma<T, LAST, S><<<grid, threads, smem, L.s>>>(P, src, dst);
+    k2_smooth_tma<T, LAST, S, MX><<<grid, threads, smem, L.s>>>(P, src, dst);
+}
+
+template <typename T, bool LAST, typename S>
+static void launch_tma_one(const Params& P, const Launch& L, const S* src, std::conditional_t<LAST, T, S>* dst) {
+    if (sizeof(T) == 4 && P.g.mx == 512) launch_tma_mx<T, LAST, S, 512>(P, L, src, dst);
+    else launch_tma_mx<T, LAST, S, 0>(P, L, src, dst);
 }
 
 // nu sweeps: ypro -> tmp -> ypro ... -> y; the iterates before y are stored as S
