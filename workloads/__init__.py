@@ -217,3 +217,35 @@ def load_arrays(problem: Problem):
     centers = np.array([ld.center for ld in problem.loads], dtype=np.float64).reshape(-1, 3)
     sigmas = np.array([ld.sigma for ld in problem.loads], dtype=np.float64)
     return kinds, params, centers, sigmas
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start: seeded draws only (initial weights and the parameter
+# vectors of the training pairs).  The network's arithmetic lives in oracle/ and
+# in the CUDA library.
+
+MLP_INIT_SEED = 4
+MLP_TRAIN_SEED = 5
+
+
+def mlp_layer_sizes(n_in: int, n_out: int, hidden: int = 128) -> Tuple[int, ...]:
+    """Widths of the warm-start network: n_in -> hidden -> hidden -> n_out."""
+    return (n_in, hidden, hidden, n_out)
+
+
+def mlp_init(sizes: Sequence[int], seed: int = MLP_INIT_SEED):
+    """Initial weights and biases, layer by layer: W_l [out][in] uniform in
+    [-a, a] with a = sqrt(6 / (in + out)) (Glorot-uniform), biases zero.
+    Returns a list of (W_l, b_l) float64 arrays."""
+    out = []
+    for l in range(len(sizes) - 1):
+        fi, fo = sizes[l], sizes[l + 1]
+        a = math.sqrt(6.0 / (fi + fo))
+        u = uniform01(seed * 1000 + l, fi * fo).reshape(fo, fi)
+        out.append(((2.0 * u - 1.0) * a, np.zeros(fo)))
+    return out
+
+
+def mlp_train_mu(w: "Workload", count: int, seed: int = MLP_TRAIN_SEED) -> np.ndarray:
+    """Parameter vectors of the warm-start training pairs (the workload's distribution)."""
+    return w.draw_mu(seed, count)
