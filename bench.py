@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --nu, --gemm as given)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no per-kernel pass, e2e, FP64 comparator or CPU baseline); for profilers")
+    ap.add_argument("--warm", action="store_true",
+                    help="also run the learned warm-start comparison (cold / Galerkin / network start)")
+    ap.add_argument("--warm-pairs", type=int, default=4096, help="training pairs (truth solves) of the network")
+    ap.add_argument("--warm-steps", type=int, default=2000, help="Adam steps of the network")
+    ap.add_argument("--warm-test", type=int, default=0, help="test queries of the comparison (default: the step's)")
     return ap.parse_args()
 
 
@@ -178,6 +183,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def warm_start_experiment(ctx, w, args, opts, dev, stream):
+    """Learned warm start: a network trained on truth solves supplies x_0 = W c(mu); the
+    comparison times each start as a whole (starting vector + RBCG) on the same test queries."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+    prob = w.problem
+    N, n = prob.n_dof, ctx.n
+    S = args.warm_pairs
+    chunk = args.batch or w.batch
+    mu_tr = wl.mlp_train_mu(w, S)
+    Y = np.zeros((S, n))
+    xb = torch.zeros((chunk, N), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    for c0 in range(0, S, chunk):
+        m = np.ascontiguousarray(mu_tr[c0:c0 + chunk])
+        ctx.pcg(m, xb[:len(m)], **opts)
+        Y[c0:c0 + len(m)] = ctx.coefficients(xb[:len(m)], stream=stream.cuda_stream)
+    pairs_s = time.perf_counter() - t0
+    del xb
+    sizes = wl.mlp_layer_sizes(prob.n_mu, n)
+    net = rb.Mlp(prob.n_mu, prob.P, sizes[1], n, rb.flatten_params(wl.mlp_init(sizes)), max_samples=S)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    hist = net.fit(mu_tr, Y, args.warm_steps, lr=3e-3, stream=stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b)
+
+    T = args.warm_test or (args.batch or w.batch)
+    mu = np.ascontiguousarray(w.draw_mu(w.test_seed, T))
+    x = torch.zeros((T, N), dtype=torch.float64, device=dev)
+    out = {"workload": w.name, "pairs": S, "pairs_solve_s": round(pairs_s, 2), "network": "x".join(map(str, sizes)),
+           "adam_steps": args.warm_steps, "train_ms": round(train_ms, 1),
+           "train_ms_per_step": round(train_ms / max(1, args.warm_steps), 4),
+           "loss_first_last": [float(hist[0]), float(hist[-1])] if len(hist) else None, "test_queries": T}
+    ref = None
+    for name in ("cold", "galerkin", "learned"):
+        kw = {**opts, "x0": name != "cold"}
+        net_arg = net if name == "learned" else None
+
+        def run():
+            if name == "cold":
+                x.zero_()   # rb_pcg zeroes x itself for a cold start; this keeps x0 visible below
+            else:
+                ctx.warm_start(mu, x, net=net_arg, stream=stream.cuda_stream)
+            return ctx.pcg(mu, x, **kw)
+
+        run()                                    # warm-up
+        if name != "cold":
+            ctx.warm_start(mu, x, net=net_arg, stream=stream.cuda_stream)
+        else:
+            x.zero_()
+        x0 = x.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status, st = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1000.0
+        if ref is None:
+            ref = x.clone()
+        err0 = ((x0 - ref).norm(dim=1) / ref.norm(dim=1)).mean().item()
+        dev_sol = ((x - ref).norm(dim=1) / ref.norm(dim=1)).max().item()
+        out[name] = {"solves_per_s": round(T / s, 1), "mean_iters": float(st["iters"].mean()),
+                     "mean_outer": float(st["outer"].mean()), "all_converged": bool(np.all(st["status"] == 0)),
+                     "max_rel_res": float(st["rel_res"].max()), "mean_initial_rel_error": err0,
+                     "max_rel_diff_to_cold_solution": dev_sol}
+    net.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -258,12 +339,15 @@ def main():
     last = stats[-1]
     ok = bool(np.all(last["status"] == rb.RB_OK))
 
+    warm = warm_start_experiment(ctx, w, args, opts, dev, stream) if args.warm and rank == 0 else None
+
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
                               "quick": True, "all_converged": ok, "mean_iters": float(last["iters"].mean()),
-                              "config": {"workload": w.name, "queries_per_step_per_gpu": B}}))
+                              "config": {"workload": w.name, "queries_per_step_per_gpu": B, "autotuned": tuned},
+                              "warm_start": warm}))
         ctx.close()
         if world > 1:
             dist.destroy_process_group()
@@ -394,6 +478,8 @@ def main():
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
             "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
         }
+        if warm is not None:
+            line["warm_start"] = warm
         print(json.dumps(line))
     ctx.close()
     if world > 1:

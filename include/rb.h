@@ -32,6 +32,7 @@ extern "C" {
 #endif
 
 typedef struct rb_ctx rb_ctx;
+typedef struct rb_mlp rb_mlp;   /* learned warm-start network (rb_mlp_create) */
 
 typedef enum {
     RB_OK = 0,
@@ -234,6 +235,86 @@ typedef struct {
 } rb_kernel_time;
 rb_status rb_profile(rb_ctx* ctx, int enable);
 rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* count);
+
+/*
+ * Starting vectors.  Alg. 2 and Alg. 3 start from x_0 = 0 but accept any x_0
+ * (rb_opts.x0_mode = RB_X0_GIVEN).  rb_warm_start writes x_b = W c_b with
+ *   net == NULL: c_b = a_N(mu_b), the Galerkin coefficients of eq. 2
+ *                (A_N(mu) a = f_N(mu), eq. 12b, Cholesky in FP64), so x_b is
+ *                the RB approximation x_hat(mu) of eq. 3;
+ *   net != NULL: c_b = the network's prediction for mu_b (rb_mlp_predict);
+ *                net must have n_in = n_mu and n_out = n of the context.
+ * The lift W c runs on FP32 copies of W and c (relative error about 1e-7; the
+ * solvers correct it).  mu host [B][n_mu] (diffusion coefficients > 0);
+ * x host or device [B][N_dof], written; coef host or device [B][n], written
+ * when not NULL.  Uses the context's workspace (not during a solve).
+ * RB_EBREAKDOWN if A_N(mu_b) is not SPD for some b (its c_b and x_b are zero).
+ */
+rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, double* x, double* coef,
+                        void* stream);
+
+/* Reduced coefficients c_b = W^T x_b of given vectors (eq. 5 applied to x
+ * instead of r): with an orthonormal W, W c_b is the orthogonal projection of
+ * x_b onto span(W).  FP32 products, FP64 sums over chunks of 32 points
+ * (relative error about 1e-7).  x host or device [B][N_dof]; coef host or
+ * device [B][n], written.  Uses the context's workspace (not during a solve). */
+rb_status rb_coefficients(rb_ctx* ctx, int B, const double* x, double* coef, void* stream);
+
+/*
+ * Learned warm start: a network c(mu) predicting reduced coefficients (the
+ * paper has no learned component; the network only supplies x_0 = W c(mu) to
+ * rb_warm_start, and the RB iterations remain the judge of its error).
+ *   features   log mu_i for i < n_log (diffusion coefficients), mu_i for
+ *              n_log <= i < n_in (load parameters), standardised by the
+ *              per-column mean and population standard deviation (floored at
+ *              1e-12) of the training set of the first fit / gradient call;
+ *   layers     n_in -> hidden -> hidden -> n_out, GELU (z Phi(z), Phi the
+ *              standard normal CDF) after both hidden layers, linear output;
+ *   output     c = out_mean + out_scale * y, out_mean / out_scale the
+ *              per-column statistics of the training targets;
+ *   precision  weights used as BF16 (FP32 masters rounded to nearest even),
+ *              biases and activations FP32, products accumulated in FP32;
+ *   training   loss = sum (y - t)^2 / (S n_out) over standardised targets t,
+ *              full batch, back-propagation, Adam (beta1 0.9, beta2 0.999,
+ *              eps 1e-8) on the FP32 masters; the gradient treats the BF16
+ *              rounding as the identity.
+ * Flat parameter vector (doubles, this order): W1 [hidden][n_in], b1 [hidden],
+ * W2 [hidden][hidden], b2 [hidden], W3 [n_out][hidden], b3 [n_out].
+ * Errors of these calls are reported by rb_last_error(NULL).  A network is not
+ * reentrant: one call at a time.
+ */
+
+/* n_in <= 32, hidden <= 128, n_out <= 128; params host [rb_mlp_num_params]
+ * (initial values); max_samples bounds S of fit / gradient and the device
+ * staging of predict.  All device memory of the network is allocated here. */
+rb_status rb_mlp_create(rb_mlp** out, int n_in, int n_log, int hidden, int n_out, const double* params,
+                        int max_samples);
+int rb_mlp_num_params(const rb_mlp* net);   /* -1 for NULL */
+
+/* steps (<= 65536) Adam steps with learning rate lr on the S training pairs:
+ * mu host [S][n_in], Y host or device [S][n_out] (target coefficients).
+ * loss host or device [steps] or NULL: the loss before each step.  The step
+ * body is replayed as a CUDA graph; synchronous. */
+rb_status rb_mlp_fit(rb_mlp* net, int S, const double* mu, const double* Y, int steps, double lr, double* loss,
+                     void* stream);
+
+/* Loss and gradient of the current parameters on S pairs (no update):
+ * loss host or device [1], grad host or device [rb_mlp_num_params] (layout of
+ * the parameter vector); either may be NULL. */
+rb_status rb_mlp_gradient(rb_mlp* net, int S, const double* mu, const double* Y, double* loss, double* grad,
+                          void* stream);
+
+/* Y [B][n_out] (host or device) = c(mu_b) for mu host [B][n_in].  Needs the
+ * standardisation of a fit or gradient call. */
+rb_status rb_mlp_predict(rb_mlp* net, int B, const double* mu, double* Y, void* stream);
+
+/* Read back the FP32 master parameters (as doubles, host [num_params]), the
+ * standardisation (host [2 n_in + 2 n_out]: in_mean, in_scale, out_mean,
+ * out_scale; zeros before the first fit) and the Adam step count.  Any pointer
+ * may be NULL. */
+rb_status rb_mlp_get(const rb_mlp* net, double* params, double* scaling, int* adam_steps);
+
+void rb_mlp_free(rb_mlp* net);
 
 /*
  * Relative residuals rel_res[b] = ||f(mu_b) - A(mu_b) x_b|| / ||f(mu_b)|| (FP64)

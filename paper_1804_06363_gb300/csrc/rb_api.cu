@@ -71,6 +71,7 @@ struct rb_ctx {
     size_t scratch_bytes = 0;
     TcPlan tc{};                      // tensor-core projection plans
     int* d_tcerr = nullptr;           // set by a tensor-core kernel whose wait expired
+    int* d_flag = nullptr;            // breakdown flag of rb_warm_start
     int nsplit_max = 1;
     bool force_generic = false;       // testing: use the generic stencil kernels everywhere
     // per-kernel timing (rb_profile)
@@ -287,6 +288,7 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     TRY(dalloc(ctx, &ctx->d_scratch, ctx->scratch_bytes / sizeof(double)));
     TRY(dalloc(ctx, &ctx->d_tcerr, 1));
     CK(cudaMemset(ctx->d_tcerr, 0, sizeof(int)));
+    TRY(dalloc(ctx, &ctx->d_flag, 1));
     TRY(tc_init(ctx->tc, ctx->geo, B, n_cap, nbp, ctx->nbp32, ctx->num_sms, ctx->d_r32, ctx->d_W32c, ctx->d_e32,
                 ctx->d_W32r, ctx->d_tcerr, ctx->err));
 
@@ -1089,6 +1091,83 @@ rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double
         launch_apply(ctx->geo, nbw, ctx->n_mu, ctx->d_mu, xs, ys, s);
         CK(cudaGetLastError());
         if (!dy) CK(cudaMemcpyAsync(y + (size_t)b0 * N, ys, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RB_OK;
+}
+
+rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, double* x, double* coef, void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!mu || !x))) { ctx->err = "B < 0 or NULL mu / x"; return RB_EINVAL; }
+    if (net && (mlp_n_in(net) != ctx->n_mu || mlp_n_out(net) != ctx->n)) {
+        ctx->err = "the network must map n_mu parameters to n coefficients of this context";
+        return RB_EINVAL;
+    }
+    if (net && !mlp_ready(net)) { ctx->err = "the network has not been fitted"; return RB_EINVAL; }
+    if (is_device_ptr(mu)) { ctx->err = "mu must be host memory"; return RB_EINVAL; }
+    for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i) {
+        if (!std::isfinite(mu[i]) || ((int)(i % ctx->n_mu) < ctx->P && !(mu[i] > 0.0))) {
+            ctx->err = "parameter vectors must be finite, with positive diffusion coefficients";
+            return RB_EINVAL;
+        }
+    }
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const int n = ctx->n;
+    const bool dx = is_device_ptr(x), dc = coef && is_device_ptr(coef);
+    LoadMap lm{};
+    for (int r = 0; r < ctx->R; ++r) lm.param[r] = ctx->load_param[r];
+    const int chunk = std::max(1, std::min<int>(ctx->Bmax, (int)(ctx->scratch_bytes / sizeof(double)) / std::max(1, n)));
+    CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int nbw = std::min(chunk, B - b0);
+        CK(cudaMemcpyAsync(ctx->d_mu, mu + (size_t)b0 * ctx->n_mu, (size_t)nbw * ctx->n_mu * sizeof(double),
+                           cudaMemcpyHostToDevice, s));
+        double* c = dc ? coef + (size_t)b0 * n : ctx->d_scratch;
+        if (n > 0) {
+            if (net) {
+                rb_status st = mlp_predict_device(net, nbw, ctx->d_mu, ctx->n_mu, c, s);
+                if (st != RB_OK) { ctx->err = "network evaluation failed"; return st; }
+            } else {
+                launch_galerkin(n, ctx->P, ctx->d_ANq, ctx->R, lm, ctx->d_fNr, ctx->n_mu, nbw, ctx->d_mu, c,
+                                ctx->d_flag, s);
+            }
+        }
+        double* xs = dx ? x + (size_t)b0 * N : ctx->d_x64;
+        launch_lift(N, n, ctx->d_W32c, nbw, c, xs, ctx->grid, s);
+        CK(cudaGetLastError());
+        if (!dx) CK(cudaMemcpyAsync(x + (size_t)b0 * N, xs, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (coef && !dc && n > 0)
+            CK(cudaMemcpyAsync(coef + (size_t)b0 * n, c, (size_t)nbw * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) { ctx->err = "A_N(mu) is not positive definite for some query"; return RB_EBREAKDOWN; }
+    return RB_OK;
+}
+
+rb_status rb_coefficients(rb_ctx* ctx, int B, const double* x, double* coef, void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!x || !coef))) { ctx->err = "B < 0 or NULL x / coef"; return RB_EINVAL; }
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const int n = ctx->n;
+    if (n == 0 || B == 0) return RB_OK;
+    const bool dx = is_device_ptr(x), dc = is_device_ptr(coef);
+    const size_t sd = ctx->scratch_bytes / sizeof(double);
+    int chunk = std::min(ctx->Bmax, 256);
+    while (chunk > 1 && (size_t)coef_splits(chunk, ctx->num_sms) * chunk * n > sd) chunk /= 2;
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int nbw = std::min(chunk, B - b0);
+        const double* xs = dx ? x + (size_t)b0 * N : ctx->d_x64;
+        if (!dx) CK(cudaMemcpyAsync(ctx->d_x64, x + (size_t)b0 * N, (size_t)nbw * N * sizeof(double),
+                                    cudaMemcpyHostToDevice, s));
+        double* c = dc ? coef + (size_t)b0 * n : ctx->d_e64;
+        launch_coefficients(N, n, ctx->d_W32c, nbw, xs, c, ctx->d_scratch, ctx->num_sms, s);
+        CK(cudaGetLastError());
+        if (!dc) CK(cudaMemcpyAsync(coef + (size_t)b0 * n, c, (size_t)nbw * n * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
     return RB_OK;

@@ -357,6 +357,24 @@ void launch_scores(const Geo& g, int P, int R, const int* load_param, int n_mu, 
                    int literal, double* score, int* bad, cudaStream_t s);
 double launch_norm(const Geo& g, const double* v, double* scratch, cudaStream_t s);
 
+// starting vectors and reduced coefficients (rb_warm_start, rb_coefficients)
+struct LoadMap {
+    int param[MAX_LOADS];        // Phi_r(mu) = mu[param[r]], or 1 when param[r] < 0
+};
+void launch_galerkin(int nb, int Q, const double* ANq, int R, const LoadMap& lm, const double* fNr, int n_mu, int B,
+                     const double* mu, double* coef, int* bad, cudaStream_t s);   // A_N(mu) a = f_N(mu)
+void launch_lift(long long n, int nb, const float* W32c, int B, const double* coef, double* x, int grid,
+                 cudaStream_t s);                                                  // x_b = W c_b
+int coef_splits(int B, int num_sms);
+void launch_coefficients(long long n, int nb, const float* W32c, int B, const double* X, double* coef,
+                         double* scratch, int num_sms, cudaStream_t s);            // c_b = W^T x_b
+
+// learned warm start (rb_mlp.cu)
+int mlp_n_in(const rb_mlp* net);
+int mlp_n_out(const rb_mlp* net);
+bool mlp_ready(const rb_mlp* net);
+rb_status mlp_predict_device(rb_mlp* net, int B, const double* d_mu, int ld_mu, double* d_out, cudaStream_t s);
+
 int tiles_flat(long long n);
 int tiles_box(const Geo& g);
 

@@ -4,6 +4,8 @@
 // CUDA-core versions, used for FP64 and as the reference engine of the mixed path.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "rb_common.cuh"
 
 namespace rbk {
@@ -426,6 +428,214 @@ void launch_scores(const Geo& g, int P_, int R, const int* load_param, int n_mu,
         configured = true;
     }
     k_scores<<<ntrain, THREADS, smem, s>>>(P_, R, load_param, n_mu, nb, ANq, fNr, Rsnap, mu, literal, score, bad);
+}
+
+}  // namespace rbk
+
+// ----------------------------------------------------------------------------
+// Starting vectors and reduced coefficients of given vectors (rb_warm_start,
+// rb_coefficients).
+
+namespace rbk {
+
+// a_N(mu) of eq. 2: A_N(mu) a = f_N(mu) with A_N(mu) = sum_q mu_q A_{N,q} and
+// f_N(mu) = sum_r Phi_r(mu) f_{N,r} (eq. 12b), by Cholesky; one CTA per query.
+// A non-positive pivot zeroes the query's coefficients and sets *bad.
+__global__ void __launch_bounds__(128) k_galerkin(int nb, int Q, const double* __restrict__ ANq, int R, LoadMap lm,
+                                                   const double* __restrict__ fNr, int n_mu,
+                                                   const double* __restrict__ mu, double* coef, int* bad) {
+    extern __shared__ double A[];      // [nb][nb], then f [nb]
+    __shared__ int brk;
+    double* f = A + (size_t)nb * nb;
+    const int q = blockIdx.x;
+    const double* m = mu + (size_t)q * n_mu;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < Q; ++t) s += m[t] * ANq[(size_t)t * nb * nb + idx];
+        A[idx] = s;
+    }
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < R; ++r) s += (lm.param[r] < 0 ? 1.0 : m[lm.param[r]]) * fNr[(size_t)r * nb + k];
+        f[k] = s;
+    }
+    if (threadIdx.x == 0) brk = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = A[j * nb + j];
+            if (!(d > 0.0)) brk = 1;
+            else A[j * nb + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (brk) break;
+        const double ljj = A[j * nb + j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i * nb + j] /= ljj;
+        __syncthreads();
+        const int rem = nb - j - 1;
+        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+            const int i = j + 1 + idx / rem, k = j + 1 + idx % rem;
+            if (k <= i) A[i * nb + k] -= A[i * nb + j] * A[k * nb + j];
+        }
+        __syncthreads();
+    }
+    double* c = coef + (size_t)q * nb;
+    if (brk) {
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) c[k] = 0.0;
+        if (threadIdx.x == 0) atomicExch(bad, 1);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        // L z = f, then L^T a = z (in place in f)
+        for (int i = 0; i < nb; ++i) {
+            double s = f[i];
+            for (int k = 0; k < i; ++k) s -= A[i * nb + k] * f[k];
+            f[i] = s / A[i * nb + i];
+        }
+        for (int i = nb - 1; i >= 0; --i) {
+            double s = f[i];
+            for (int k = i + 1; k < nb; ++k) s -= A[k * nb + i] * f[k];
+            f[i] = s / A[i * nb + i];
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) c[k] = f[k];
+}
+
+void launch_galerkin(int nb, int Q, const double* ANq, int R, const LoadMap& lm, const double* fNr, int n_mu, int B,
+                     const double* mu, double* coef, int* bad, cudaStream_t s) {
+    if (nb == 0 || B == 0) return;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (MAX_N * MAX_N + MAX_N) * 8);
+        configured = true;
+    }
+    k_galerkin<<<B, 128, (size_t)(nb * nb + nb) * sizeof(double), s>>>(nb, Q, ANq, R, lm, fNr, n_mu, mu, coef, bad);
+}
+
+// x_b = W c_b for B queries (FP32 products and sums, written as FP64): one pass
+// over W per group of LQ queries, points coalesced.
+constexpr int LQ = 16;
+
+__global__ void __launch_bounds__(THREADS) k_lift(long long n, int nb, const float* __restrict__ Wc, int B,
+                                                  const double* __restrict__ coef, double* __restrict__ x) {
+    __shared__ float cs[LQ][MAX_N];
+    const int groups = (B + LQ - 1) / LQ;
+    const long long chunks = (n + TILE - 1) / TILE;
+    for (long long w = blockIdx.x; w < (long long)groups * chunks; w += gridDim.x) {
+        const int grp = (int)(w / chunks);
+        const long long ch = w % chunks;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < LQ * nb; idx += THREADS) {
+            const int g = idx / nb, k = idx % nb, b = grp * LQ + g;
+            cs[g][k] = b < B ? (float)coef[(size_t)b * nb + k] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int j = 0; j < TILE / THREADS; ++j) {
+            const long long i = ch * TILE + (long long)j * THREADS + threadIdx.x;
+            if (i >= n) continue;
+            float acc[LQ];
+#pragma unroll
+            for (int g = 0; g < LQ; ++g) acc[g] = 0.0f;
+            for (int k = 0; k < nb; ++k) {
+                const float wv = Wc[(size_t)k * n + i];
+#pragma unroll
+                for (int g = 0; g < LQ; ++g) acc[g] = fmaf(cs[g][k], wv, acc[g]);
+            }
+#pragma unroll
+            for (int g = 0; g < LQ; ++g) {
+                const int b = grp * LQ + g;
+                if (b < B) x[(size_t)b * n + i] = (double)acc[g];
+            }
+        }
+    }
+}
+
+void launch_lift(long long n, int nb, const float* W32c, int B, const double* coef, double* x, int grid,
+                 cudaStream_t s) {
+    if (B == 0) return;
+    if (nb == 0) {
+        cudaMemsetAsync(x, 0, (size_t)B * n * sizeof(double), s);
+        return;
+    }
+    k_lift<<<grid, THREADS, 0, s>>>(n, nb, W32c, B, coef, x);
+}
+
+// part[sp][b][k] = sum over split sp of W[i][k] x_b[i]: FP32 products summed in
+// FP32 over chunks of CPC points, chunk sums added in FP64.
+constexpr int CQ = 8;
+constexpr int CPC = 32;
+
+__global__ void __launch_bounds__(THREADS) k_coef_part(long long n, int nb, const float* __restrict__ Wc, int B,
+                                                       const double* __restrict__ X, int nsplit, double* part) {
+    __shared__ float Ws[CPC][MAX_N + 1];
+    __shared__ float Xs[CQ][CPC];
+    const int groups = (B + CQ - 1) / CQ;
+    const long long span = ((n + nsplit - 1) / nsplit + CPC - 1) / CPC * CPC;
+    for (long long w = blockIdx.x; w < (long long)groups * nsplit; w += gridDim.x) {
+        const int grp = (int)(w / nsplit), sp = (int)(w % nsplit);
+        const long long i0 = (long long)sp * span;
+        const long long i1 = i0 + span < n ? i0 + span : n;
+        double acc[CQ * MAX_N / THREADS];
+#pragma unroll
+        for (int j = 0; j < CQ * MAX_N / THREADS; ++j) acc[j] = 0.0;
+        for (long long c0 = i0; c0 < i1; c0 += CPC) {
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nb * CPC; idx += THREADS) {
+                const int k = idx / CPC, i = idx % CPC;
+                Ws[i][k] = c0 + i < i1 ? Wc[(size_t)k * n + c0 + i] : 0.0f;
+            }
+            for (int idx = threadIdx.x; idx < CQ * CPC; idx += THREADS) {
+                const int g = idx / CPC, i = idx % CPC, b = grp * CQ + g;
+                Xs[g][i] = (b < B && c0 + i < i1) ? (float)X[(size_t)b * n + c0 + i] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < CQ * MAX_N / THREADS; ++j) {
+                const int o = threadIdx.x + j * THREADS;
+                if (o < CQ * nb) {
+                    const int g = o / nb, k = o % nb;
+                    float a = 0.0f;
+#pragma unroll 8
+                    for (int i = 0; i < CPC; ++i) a = fmaf(Ws[i][k], Xs[g][i], a);
+                    acc[j] += (double)a;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CQ * MAX_N / THREADS; ++j) {
+            const int o = threadIdx.x + j * THREADS;
+            if (o < CQ * nb) {
+                const int g = o / nb, k = o % nb, b = grp * CQ + g;
+                if (b < B) part[((size_t)sp * B + b) * nb + k] = acc[j];
+            }
+        }
+    }
+}
+
+__global__ void k_coef_sum(int nsplit, int B, int nb, const double* __restrict__ part, double* coef) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * nb) return;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(size_t)sp * B * nb + idx];
+    coef[idx] = s;
+}
+
+// coef [B][nb] = W^T X_b; scratch must hold coef_splits(B, num_sms) * B * nb doubles
+int coef_splits(int B, int num_sms) {
+    const int groups = (B + CQ - 1) / CQ;
+    return std::max(1, std::min(64, (4 * num_sms + groups - 1) / groups));
+}
+
+void launch_coefficients(long long n, int nb, const float* W32c, int B, const double* X, double* coef,
+                         double* scratch, int num_sms, cudaStream_t s) {
+    if (B == 0 || nb == 0) return;
+    const int nsplit = coef_splits(B, num_sms);
+    const long long work = (long long)((B + CQ - 1) / CQ) * nsplit;
+    const int grid = (int)std::min<long long>(work, 8LL * num_sms);
+    k_coef_part<<<grid, THREADS, 0, s>>>(n, nb, W32c, B, X, nsplit, scratch);
+    k_coef_sum<<<(B * nb + 255) / 256, 256, 0, s>>>(nsplit, B, nb, scratch, coef);
 }
 
 }  // namespace rbk

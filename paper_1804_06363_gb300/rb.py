@@ -86,6 +86,17 @@ SIGNATURES = {
     "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
     "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "rb_warm_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_coefficients": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "rb_mlp_num_params": (C.c_int, [C.c_void_p]),
+    "rb_mlp_fit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                             C.c_void_p]),
+    "rb_mlp_gradient": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "rb_mlp_predict": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_mlp_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "rb_mlp_free": (None, [C.c_void_p]),
     "rb_last_error": (C.c_char_p, [C.c_void_p]),
     "rb_status_string": (C.c_char_p, [C.c_int]),
     "rb_free": (None, [C.c_void_p]),
@@ -202,6 +213,98 @@ def residual_noalloc(prob, mu, x, stream: Optional[int] = None) -> np.ndarray:
     if st != RB_OK:
         raise RbError(st, lib().rb_last_error(None).decode())
     return out
+
+
+def flatten_params(layers) -> np.ndarray:
+    """The flat parameter vector of rb_mlp_create from [(W_1, b_1), (W_2, b_2), (W_3, b_3)],
+    W_l [out][in] (concatenation in the header's order)."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64).ravel()])
+                           for W, b in layers])
+
+
+def unflatten_params(flat, sizes):
+    """Inverse of flatten_params for layer widths sizes = (n_in, hidden, hidden, n_out)."""
+    out, o = [], 0
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        W = flat[o:o + fi * fo].reshape(fo, fi)
+        o += fi * fo
+        b = flat[o:o + fo]
+        o += fo
+        out.append((W.copy(), b.copy()))
+    return out
+
+
+class Mlp:
+    """The warm-start network (rb_mlp*): n_in -> hidden -> hidden -> n_out, BF16 weights."""
+
+    def __init__(self, n_in: int, n_log: int, hidden: int, n_out: int, params, max_samples: int):
+        flat = _f64(params)
+        self.sizes = (n_in, hidden, hidden, n_out)
+        self._h = C.c_void_p()
+        st = lib().rb_mlp_create(C.byref(self._h), n_in, n_log, hidden, n_out, _ptr(flat), max_samples)
+        if st != RB_OK:
+            raise RbError(st, lib().rb_last_error(None).decode())
+        self.num_params = lib().rb_mlp_num_params(self._h)
+        if self.num_params != flat.size:
+            expected = self.num_params
+            self.close()
+            raise ValueError(f"expected {expected} parameters, got {flat.size}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, st):
+        if st != RB_OK:
+            raise RbError(st, lib().rb_last_error(None).decode())
+
+    def fit(self, mu, Y, steps: int, lr: float = 3e-3, stream: Optional[int] = None) -> np.ndarray:
+        """rb_mlp_fit: Adam steps on the pairs (mu host [S][n_in], Y host or device [S][n_out]);
+        returns the loss before each step."""
+        mu = _f64(mu)
+        Y = _f64(Y) if isinstance(Y, np.ndarray) else Y
+        loss = np.zeros(max(steps, 1))
+        self._check(lib().rb_mlp_fit(self._h, mu.shape[0], _ptr(mu), _ptr(Y), steps, lr, _ptr(loss),
+                                     C.c_void_p(int(stream) if stream else 0)))
+        return loss[:steps]
+
+    def gradient(self, mu, Y, stream: Optional[int] = None):
+        """rb_mlp_gradient: (loss, flat gradient) of the current parameters."""
+        mu = _f64(mu)
+        Y = _f64(Y) if isinstance(Y, np.ndarray) else Y
+        loss = np.zeros(1)
+        grad = np.zeros(self.num_params)
+        self._check(lib().rb_mlp_gradient(self._h, mu.shape[0], _ptr(mu), _ptr(Y), _ptr(loss), _ptr(grad),
+                                          C.c_void_p(int(stream) if stream else 0)))
+        return float(loss[0]), grad
+
+    def predict(self, mu, out=None, stream: Optional[int] = None):
+        """rb_mlp_predict: coefficients [B][n_out] (host array unless a device out is given)."""
+        mu = _f64(mu).reshape(-1, self.sizes[0])
+        if out is None:
+            out = np.zeros((mu.shape[0], self.sizes[-1]))
+        self._check(lib().rb_mlp_predict(self._h, mu.shape[0], _ptr(mu), _ptr(out),
+                                         C.c_void_p(int(stream) if stream else 0)))
+        return out
+
+    def get(self):
+        """rb_mlp_get: (flat FP32 master parameters, standardisation, Adam steps)."""
+        p = np.zeros(self.num_params)
+        sc = np.zeros(2 * self.sizes[0] + 2 * self.sizes[-1])
+        t = C.c_int()
+        self._check(lib().rb_mlp_get(self._h, _ptr(p), _ptr(sc), C.byref(t)))
+        return p, sc, t.value
+
+    def close(self) -> None:
+        if self._h:
+            lib().rb_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:
@@ -325,6 +428,22 @@ class Context:
         return {"nu": r.nu, "inner_tol": r.inner_tol, "gemm": inv.get(r.gemm, r.gemm),
                 "ms_per_solve": r.ms_per_solve, "trials": r.trials, "kernels": r.kernels,
                 "store": {v: k for k, v in STORES.items()}.get(r.store, r.store)}
+
+    def warm_start(self, mu, x, net: Optional[Mlp] = None, coef=None, stream: Optional[int] = None) -> int:
+        """rb_warm_start: x [B][N_dof] (host or device) = W c(mu), c = Galerkin coefficients (net None)
+        or the network's prediction; coef [B][n] receives c when given."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        return self._check(lib().rb_warm_start(self._h, net.handle if net is not None else None, mu.shape[0],
+                                               _ptr(mu), _ptr(x), _ptr(coef),
+                                               C.c_void_p(int(stream) if stream else 0)))
+
+    def coefficients(self, x, coef=None, stream: Optional[int] = None):
+        """rb_coefficients: W^T x_b for x [B][N_dof] (host or device); returns coef (host unless given)."""
+        B = x.shape[0]
+        if coef is None:
+            coef = np.zeros((B, self.n))
+        self._check(lib().rb_coefficients(self._h, B, _ptr(x), _ptr(coef), C.c_void_p(int(stream) if stream else 0)))
+        return coef
 
     def profile(self, enable: bool) -> None:
         """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""

@@ -68,3 +68,19 @@ def test_invalid_problem_is_rejected_without_gpu(libpath):
     st = rb.lib().rb_offline_load_arrays(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, 1)
     assert st == rb.RB_EINVAL and not h.value
     assert b"dim" in rb.lib().rb_last_error(None)
+
+
+def test_network_and_warm_start_arguments_are_validated_without_gpu(libpath):
+    """rb_mlp_create checks its sizes, rb_warm_start / rb_coefficients their context, before any CUDA call."""
+    from paper_1804_06363_gb300 import rb
+    lib = rb.lib()
+    h = ctypes.c_void_p()
+    params = (ctypes.c_double * 8)()
+    for args in ((0, 0, 8, 4), (33, 0, 8, 4), (4, 5, 8, 4), (4, 2, 129, 4), (4, 2, 8, 129), (4, 2, 0, 4)):
+        st = lib.rb_mlp_create(ctypes.byref(h), *args, params, 16)
+        assert st == rb.RB_EINVAL and not h.value, args
+    assert b"sizes" in lib.rb_last_error(None)
+    assert lib.rb_mlp_num_params(None) == -1
+    assert lib.rb_warm_start(None, None, 1, None, None, None, None) == rb.RB_EINVAL
+    assert lib.rb_coefficients(None, 1, None, None, None) == rb.RB_EINVAL
+    lib.rb_mlp_free(None)

@@ -1,0 +1,172 @@
+"""GPU parity of the learned warm start and of the starting vectors.
+
+* the network kernels (standardisation, forward pass, back-propagation, Adam)
+  against the FP64 oracle of oracle/mlp.py on the same BF16-rounded weights;
+* rb_warm_start without a network against the oracle's Galerkin approximation
+  (eqs. 2-3), rb_coefficients against W^T x;
+* a trained network's start against the cold start of RBCG (Alg. 3): every
+  start reaches the same solution (relative L2 1e-9 of the oracle's truth at
+  relative residual 1e-10), and the test reports what the network gains.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import direct, greedy, mlp
+from oracle import rb as orb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1804_06363_gb300 import rb  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def _net_case(n_in, P, hidden, n_out, S, seed):
+    """Initial parameters (Glorot weights, small random biases), parameter vectors of a
+    workload-like distribution and random targets with offsets and unequal scales."""
+    sizes = (n_in, hidden, hidden, n_out)
+    rng = np.random.default_rng(seed)
+    layers = [(W, 0.1 * rng.standard_normal(W.shape[0])) for W, _ in wl.mlp_init(sizes, seed)]
+    u = wl.uniform01(100 + seed, S * n_in).reshape(S, n_in)
+    mu = u.copy()
+    mu[:, :P] = np.exp(np.log(0.1) + u[:, :P] * np.log(100.0))
+    Y = rng.standard_normal((S, n_out)) * rng.uniform(0.1, 3.0, n_out) + rng.uniform(-2, 2, n_out)
+    return sizes, layers, mu, Y
+
+
+@pytest.mark.parametrize("n_in,P,hidden,n_out,S", [(11, 9, 128, 40, 100), (3, 2, 48, 7, 37), (8, 8, 128, 60, 64)])
+def test_gradient_and_standardisation_match_oracle(n_in, P, hidden, n_out, S):
+    sizes, layers, mu, Y = _net_case(n_in, P, hidden, n_out, S, seed=7)
+    net = rb.Mlp(n_in, P, hidden, n_out, rb.flatten_params(layers), max_samples=S)
+    loss, g = net.gradient(mu, Y)
+    _, scale, t = net.get()
+    assert t == 0
+    onet = mlp.from_init(layers, mlp.features(mu, P), Y)
+    np.testing.assert_allclose(scale, np.concatenate([onet.in_mean, onet.in_scale, onet.out_mean, onet.out_scale]),
+                               rtol=1e-12, atol=1e-14)
+    X = (mlp.features(mu, P) - onet.in_mean) / onet.in_scale
+    Ts = (Y - onet.out_mean) / onet.out_scale
+    oloss, gW, gb = mlp.loss_and_grads(onet, X, Ts, rounding=True)
+    assert abs(loss - oloss) <= 1e-5 * oloss, (loss, oloss)
+    got = rb.unflatten_params(g, sizes)
+    for l in range(3):
+        assert _rel(got[l][0], gW[l]) < 1e-4, ("W", l, _rel(got[l][0], gW[l]))
+        assert _rel(got[l][1], gb[l]) < 1e-4, ("b", l, _rel(got[l][1], gb[l]))
+    net.close()
+
+
+def test_adam_training_and_inference_match_oracle():
+    n_in, P, hidden, n_out, S = 11, 9, 128, 40, 200
+    sizes, layers, mu, Y = _net_case(n_in, P, hidden, n_out, S, seed=11)
+    net = rb.Mlp(n_in, P, hidden, n_out, rb.flatten_params(layers), max_samples=S)
+    steps = 40                         # two replays of the captured 16-step graph and 8 direct steps
+    hist = net.fit(mu, Y, steps, lr=3e-3)
+    onet = mlp.from_init(layers, mlp.features(mu, P), Y)
+    ohist = mlp.train(onet, mlp.features(mu, P), Y, steps, lr=3e-3)
+    np.testing.assert_allclose(hist, ohist, rtol=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    # inference on new parameters with the trained masters: the oracle rounds the
+    # same FP32 masters to the same BF16 weights
+    flat, scale, t = net.get()
+    assert t == steps
+    trained = rb.unflatten_params(flat, sizes)
+    onet2 = mlp.Net([W for W, _ in trained], [b for _, b in trained], scale[:n_in], scale[n_in:2 * n_in],
+                    scale[2 * n_in:2 * n_in + n_out], scale[2 * n_in + n_out:])
+    _, _, mu_new, _ = _net_case(n_in, P, hidden, n_out, 77, seed=12)
+    pred = net.predict(mu_new)
+    ref = mlp.predict(onet2, mu_new, P)
+    assert np.max(np.abs(pred - ref) / onet2.out_scale) < 2e-5
+    # device output buffer, same values
+    out = torch.zeros((77, n_out), dtype=torch.float64, device="cuda")
+    net.predict(mu_new, out=out)
+    np.testing.assert_allclose(out.cpu().numpy(), pred, rtol=0, atol=0)
+    net.close()
+
+
+@pytest.fixture(scope="module")
+def case2d():
+    w = wl.small((40, 36), (3, 3), n_basis=8, n_train=40, bumps=True)
+    basis = greedy.greedy(w.problem, w.train_mu(), w.n_basis)
+    ctx = rb.Context.from_arrays(w.problem, basis.W, basis.ANq, basis.fNr, max_batch=5)
+    yield w, basis, ctx
+    ctx.close()
+
+
+def test_galerkin_start_matches_oracle(case2d):
+    w, basis, ctx = case2d
+    mu = w.test_mu(7)                                  # two chunks of the 5-query workspace
+    ref_c = np.stack([orb.rb_coefficients(basis, m) for m in mu])
+    for on_device in (False, True):
+        if on_device:
+            x = torch.zeros((7, w.problem.n_dof), dtype=torch.float64, device="cuda")
+            c = torch.zeros((7, basis.N), dtype=torch.float64, device="cuda")
+        else:
+            x, c = np.zeros((7, w.problem.n_dof)), np.zeros((7, basis.N))
+        assert ctx.warm_start(mu, x, coef=c) == rb.RB_OK
+        xs = x.cpu().numpy() if on_device else x
+        cs = c.cpu().numpy() if on_device else c
+        for b in range(7):
+            assert _rel(cs[b], ref_c[b]) < 1e-11
+            assert _rel(xs[b], basis.W @ ref_c[b]) < 1e-6       # FP32 lift
+    bad = mu[:1].copy()
+    bad[0, 0] = -1.0                                     # A(mu) would not be SPD: rejected before any launch
+    with pytest.raises(rb.RbError):
+        ctx.warm_start(bad, np.zeros((1, w.problem.n_dof)))
+
+
+def test_coefficients_match_projection(case2d):
+    w, basis, ctx = case2d
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((6, w.problem.n_dof))
+    c = ctx.coefficients(x)
+    cd = ctx.coefficients(torch.as_tensor(x, device="cuda"))
+    ref = x @ basis.W
+    for b in range(6):
+        assert _rel(c[b], ref[b]) < 1e-6
+    np.testing.assert_array_equal(c, cd)
+
+
+def test_learned_warm_start_reaches_truth_and_reports_gain():
+    """3D 24^3, P = 8, n = 12: network trained on 512 truth solves, 48 test queries."""
+    w = wl.small((24, 24, 24), (2, 2, 2), n_basis=12, n_train=96)
+    prob = w.problem
+    S, T = 512, 48
+    ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=S)
+    n = ctx.n
+    mu_tr = wl.mlp_train_mu(w, S)
+    x_tr = torch.zeros((S, prob.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu_tr, x_tr, precision="mixed")
+    assert status == rb.RB_OK
+    Y = ctx.coefficients(x_tr)
+    sizes = wl.mlp_layer_sizes(prob.n_mu, n)
+    net = rb.Mlp(prob.n_mu, prob.P, sizes[1], n, rb.flatten_params(wl.mlp_init(sizes)), max_samples=S)
+    hist = net.fit(mu_tr, Y, 1500, lr=3e-3)
+    assert hist[-1] < 0.02 * hist[0], (hist[0], hist[-1])
+
+    mu = w.test_mu(T)
+    truth = np.stack([direct.sparse_direct(prob, m) for m in mu[:4]])
+    runs = {}
+    for name in ("cold", "galerkin", "learned"):
+        x = torch.zeros((T, prob.n_dof), dtype=torch.float64, device="cuda")
+        if name != "cold":
+            ctx.warm_start(mu, x, net=net if name == "learned" else None)
+        x0 = x.cpu().numpy()
+        status, st = ctx.pcg(mu, x, precision="mixed", x0=name != "cold")
+        assert status == rb.RB_OK and np.all(st["rel_res"] < 1e-10), name
+        xs = x.cpu().numpy()
+        for b in range(4):
+            assert _rel(xs[b], truth[b]) < 1e-9, (name, b)
+        runs[name] = (x0, xs, st)
+    ref = runs["cold"][1]
+    err0 = {k: float(np.mean([_rel(v[0][b], ref[b]) for b in range(T)])) for k, v in runs.items()}
+    its = {k: float(v[2]["iters"].mean()) for k, v in runs.items()}
+    print("\nwarm start, 24^3 P=8 n=%d: mean initial error %s; mean inner iterations %s" % (n, err0, its))
+    assert err0["cold"] == 1.0
+    assert err0["learned"] < 0.1 and err0["galerkin"] < 0.1
+    assert its["learned"] <= its["cold"] + 1.0
+    net.close()
+    ctx.close()
