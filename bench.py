@@ -183,6 +183,15 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def progress(msg: str) -> None:
+    """One line of progress on stderr (the JSON result goes to stdout)."""
+    sys.stderr.write("[bench %.1fs] %s\n" % (time.perf_counter() - T_START, msg))
+    sys.stderr.flush()
+
+
+T_START = time.perf_counter()
+
+
 def warm_start_experiment(ctx, w, args, opts, dev, stream):
     """Learned warm start: a network trained on truth solves supplies x_0 = W c(mu); the
     comparison times each start as a whole (starting vector + RBCG) on the same test queries."""
@@ -204,6 +213,7 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
         ctx.pcg(m, xb[:len(m)], **opts)
         Y[c0:c0 + len(m)] = ctx.coefficients(xb[:len(m)], stream=stream.cuda_stream)
     pairs_s = time.perf_counter() - t0
+    progress(f"warm start: {S} truth solves and their coefficients in {pairs_s:.1f} s")
     del xb
     sizes = wl.mlp_layer_sizes(prob.n_mu, n)
     net = rb.Mlp(prob.n_mu, prob.P, sizes[1], n, rb.flatten_params(wl.mlp_init(sizes)), max_samples=S)
@@ -214,6 +224,7 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
     b.record(stream)
     torch.cuda.synchronize()
     train_ms = a.elapsed_time(b)
+    progress(f"warm start: {args.warm_steps} Adam steps in {train_ms:.0f} ms, loss {hist[0]:.3g} -> {hist[-1]:.3g}")
 
     T = args.warm_test or (args.batch or w.batch)
     mu = np.ascontiguousarray(w.draw_mu(w.test_seed, T))
@@ -255,6 +266,7 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
                      "mean_outer": float(st["outer"].mean()), "all_converged": bool(np.all(st["status"] == 0)),
                      "max_rel_res": float(st["rel_res"].max()), "mean_initial_rel_error": err0,
                      "max_rel_diff_to_cold_solution": dev_sol}
+        progress(f"warm start: {name}: {out[name]}")
     net.close()
     return out
 
@@ -291,6 +303,7 @@ def main():
         if args.basis:
             ctx.save(args.basis)
     offline_s = time.perf_counter() - t0
+    progress(f"basis of {w.name} ready in {offline_s:.1f} s")
     _, _, _, _, sel = ctx.basis()
 
     # weak scaling: every rank solves its own B test parameters (replicas, no data-path collective)
@@ -310,6 +323,7 @@ def main():
         opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
                     store=tuned["store"])
         tuned["sample"] = f"{tB} training parameters"
+        progress(f"autotuned: {tuned}")
 
     def step(xbuf, **kw):
         status, st = ctx.pcg(mu, xbuf, **{**opts, **kw})
@@ -337,6 +351,7 @@ def main():
         dist.barrier()
     value = world * B * args.steps / t_max
     last = stats[-1]
+    progress(f"timed steps: {value:.1f} solves/s, mean iterations {float(last['iters'].mean()):.1f}")
     ok = bool(np.all(last["status"] == rb.RB_OK))
 
     warm = warm_start_experiment(ctx, w, args, opts, dev, stream) if args.warm and rank == 0 else None

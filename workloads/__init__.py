@@ -202,6 +202,7 @@ WORKLOADS = {
     "rbi_2d_64": rbi_2d_64,
     "rbcg_2d_512": rbcg_2d_512,
     "batched_3d_128": batched_3d_128,
+    "batched_3d_64": lambda: ragged_3d(64),
     "large_3d_256": large_3d_256,
 }
 
