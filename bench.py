@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--nu", type=int, default=1)
     ap.add_argument("--gemm", default="auto")
+    ap.add_argument("--kernels", type=int, default=0, help="stencil kernel family (rb_opts.kernels)")
     ap.add_argument("--fp64-queries", type=int, default=256, help="queries of the FP64 plain comparator (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=300,
@@ -313,7 +314,8 @@ def main():
     mu = np.ascontiguousarray(mu_all[lo:hi])
     x = torch.zeros((B, N), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, stream=stream.cuda_stream)
+    opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, kernels=args.kernels,
+                stream=stream.cuda_stream)
 
     # ---- autotuner (setup, not timed): on training parameters, never on the timed test queries
     tuned = None

@@ -85,13 +85,14 @@ typedef struct {
     int max_outer;      /* mixed: maximum FP64 refinement steps */
     int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
     int graph;          /* 1: replay the iteration body as a captured CUDA graph */
-    int kernels;        /* stencil kernels on 2D grids whose rows hold a multiple of 128 points
-                           (other grids always take the generic kernels):
+    int kernels;        /* stencil kernels on 2D grids whose rows hold a multiple of 128 points:
                            0: CG body and one smoother pass per sweep with rows staged in shared
                               memory by bulk asynchronous copies;
                            1: as 0, but all red-black sweeps fused in one pass (FP32 mixed path,
                               nu <= 6);
-                           2: CG body and one smoother pass per sweep with rows held in registers */
+                           2: CG body and one smoother pass per sweep with rows held in registers.
+                           On 3D grids 0 and 1 select the red-black smoother that marches in z
+                           (RBCG), 2 the generic one.  Other grids take the generic kernels. */
     int store;          /* RB_STORE_*: storage of the preconditioner's intermediate vectors (the
                            prolongation W e_N and the smoother sweeps before the last one).
                            RB_STORE_BF16 halves their bytes; the arithmetic stays FP32 and the

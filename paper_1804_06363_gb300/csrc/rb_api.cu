@@ -544,6 +544,7 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
     cudaStream_t s = L.s;
     const bool rm = use_rowmarch(ctx->geo) && !ctx->force_generic;
+    const bool zm = use_zmarch_smoother(ctx->geo) && !ctx->force_generic;
     if (m.mixed) {
         if (use_tc) {
             timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
@@ -561,6 +562,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels != 2) launch3d_smooth<float>(P, L, o.nu);
             else launch_smoother<float>(P, L, o.nu, false);
         });
     } else {
@@ -571,6 +573,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<double>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels != 2) launch3d_smooth<double>(P, L, o.nu);
             else launch_smoother<double>(P, L, o.nu, false);
         });
     }
@@ -1036,7 +1039,8 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             const double ms = trial(t);
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
-        if (best.smoother == RB_SMOOTH_RBGS && use_rowmarch(ctx->geo) && !ctx->force_generic) {
+        if (best.smoother == RB_SMOOTH_RBGS && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
+            !ctx->force_generic) {
             const rb_opts base = best;
             for (int kk = 0; kk <= 2; ++kk) {
                 if (kk == base.kernels || (kk == 1 && !use_fused_smoother(ctx->geo, base.nu))) continue;

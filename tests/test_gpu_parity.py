@@ -362,6 +362,36 @@ def test_batched_products_both_engines(dims, n):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,blocks,nu", [((70, 19, 20), (2, 2, 2), 1), ((33, 9, 17), (3, 1, 2), 2),
+                                             ((64, 16, 32), (2, 2, 2), 3)])
+def test_zmarch_smoother_matches_generic_and_oracle(dims, blocks, nu):
+    """The 3D smoother marching in z (kernels 0: 32 x 8 tiles, 16-plane chunks, ragged at every edge
+    here) applies the same preconditioner as the generic one (kernels 2), the FP64 one agrees with the
+    oracle's RBI(A, r, W, 1) (eqs. 5-8), and RBCG with it reaches the truth."""
+    w = wl.small(dims, blocks, n_basis=5, n_train=20, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    r = np.random.default_rng(4).standard_normal((3, prob.n_dof))
+    for precision, dt, tol in (("fp64", np.float64, 1e-13), ("mixed", np.float32, 1e-6)):
+        rr = r.astype(dt)
+        y0 = ctx.precondition(mu, rr, precision=precision, nu=nu, kernels=0, gemm="cuda_cores")
+        y2 = ctx.precondition(mu, rr, precision=precision, nu=nu, kernels=2, gemm="cuda_cores")
+        assert np.abs(y0 - y2).max() <= tol * np.abs(y2).max(), precision
+    ref = np.stack([orb.rbi_precondition(basis, mu[b], orb.reduced_factor(basis, mu[b]), r[b], "rbgs", nu)
+                    for b in range(3)])
+    y64 = ctx.precondition(mu, r, precision="fp64", nu=nu, kernels=0)
+    assert np.abs(y64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    for precision in ("fp64", "mixed"):
+        x = torch.zeros((3, prob.n_dof), dtype=torch.float64, device="cuda")
+        status, st = ctx.pcg(mu, x, precision=precision, nu=nu, kernels=0)
+        assert status == rb.RB_OK, (precision, st)
+        for b in range(3):
+            assert _rel(x[b].cpu().numpy(), direct.sparse_direct(prob, mu[b])) < 1e-9, (precision, b)
+    ctx.close()
+
+
 def test_3d_fp64_and_mixed():
     w = wl.small((14, 12, 10), (2, 2, 2), n_basis=6, n_train=24)
     prob = w.problem
