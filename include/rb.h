@@ -91,8 +91,10 @@ typedef struct {
                            1: as 0, but all red-black sweeps fused in one pass (FP32 mixed path,
                               nu <= 6);
                            2: CG body and one smoother pass per sweep with rows held in registers.
-                           On 3D grids 0 and 1 select the red-black smoother that marches in z
-                           (RBCG), 2 the generic one.  Other grids take the generic kernels. */
+                           On 3D grids (RBCG): 0 marches the CG body and the red-black smoother in
+                           z with planes prefetched into shared memory by asynchronous copies;
+                           1 the smoother marching in z with direct loads and the generic CG
+                           body; 2 the generic kernels.  Other grids take the generic kernels. */
     int store;          /* RB_STORE_*: storage of the preconditioner's intermediate vectors (the
                            prolongation W e_N and the smoother sweeps before the last one).
                            RB_STORE_BF16 halves their bytes; the arithmetic stays FP32 and the

@@ -514,26 +514,31 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
     enqueue_prec(ctx, P, L, o, m, use_tc);
     cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
     const bool staged = rm && o.kernels != 2 && use_staged_cg(ctx->geo);
+    const bool z3 = use_zmarch_smoother(ctx->geo) && !ctx->force_generic && o.kernels == 0;
     if (m.mixed) {
         timed(ctx, KK_CG_A, s, [&] {
             if (staged) launch2d_cg_a_staged<float>(P, L);
             else if (rm) launch2d_cg_a<float>(P, L);
+            else if (z3) launch3d_cg_a<float>(P, L);
             else launch_cg_a<float>(P, L);
         });
         timed(ctx, KK_CG_B, s, [&] {
             if (staged) launch2d_cg_b_staged<float>(P, L);
             else if (rm) launch2d_cg_b<float>(P, L);
+            else if (z3) launch3d_cg_b<float>(P, L);
             else launch_cg_b<float>(P, L);
         });
     } else {
         timed(ctx, KK_CG_A, s, [&] {
             if (staged) launch2d_cg_a_staged<double>(P, L);
             else if (rm) launch2d_cg_a<double>(P, L);
+            else if (z3) launch3d_cg_a<double>(P, L);
             else launch_cg_a<double>(P, L);
         });
         timed(ctx, KK_CG_B, s, [&] {
             if (staged) launch2d_cg_b_staged<double>(P, L);
             else if (rm) launch2d_cg_b<double>(P, L);
+            else if (z3) launch3d_cg_b<double>(P, L);
             else launch_cg_b<double>(P, L);
         });
     }
@@ -562,7 +567,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
-            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels != 2) launch3d_smooth<float>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0) launch3d_smooth_staged<float>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1) launch3d_smooth<float>(P, L, o.nu);
             else launch_smoother<float>(P, L, o.nu, false);
         });
     } else {
@@ -573,7 +579,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<double>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
-            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels != 2) launch3d_smooth<double>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0) launch3d_smooth_staged<double>(P, L, o.nu);
+            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1) launch3d_smooth<double>(P, L, o.nu);
             else launch_smoother<double>(P, L, o.nu, false);
         });
     }
@@ -1043,7 +1050,8 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             !ctx->force_generic) {
             const rb_opts base = best;
             for (int kk = 0; kk <= 2; ++kk) {
-                if (kk == base.kernels || (kk == 1 && !use_fused_smoother(ctx->geo, base.nu))) continue;
+                if (kk == base.kernels || (kk == 1 && ctx->geo.dim == 2 && !use_fused_smoother(ctx->geo, base.nu)))
+                    continue;
                 if (kk != 0 && base.store == RB_STORE_BF16) continue;   // BF16 iterates need kernels = 0
                 rb_opts t = base;
                 t.kernels = kk;

@@ -340,9 +340,13 @@ template <typename T> void launch2d_smooth_tma(const Params& P, const Launch& L,
 bool use_fused_smoother(const Geo& g, int nu);
 void launch2d_smooth_fused(const Params& P, const Launch& L, int nu);
 int fused_tiles(const Geo& g, int nu);
-// 3D red-black smoother marching in z (PCG mode; tiles of 32 x 8 x 16)
+// 3D kernels marching in z (PCG mode; tiles of 32 x 8 x 16): the red-black smoother with
+// direct loads, and the smoother and CG body with planes prefetched by asynchronous copies
 bool use_zmarch_smoother(const Geo& g);
 template <typename T> void launch3d_smooth(const Params& P, const Launch& L, int nu);
+template <typename T> void launch3d_smooth_staged(const Params& P, const Launch& L, int nu);
+template <typename T> void launch3d_cg_a(const Params& P, const Launch& L);
+template <typename T> void launch3d_cg_b(const Params& P, const Launch& L);
 template <typename T> void launch_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch_cg_b(const Params& P, const Launch& L);
 void launch_rbi_residual(const Params& P, const Launch& L);

@@ -147,9 +147,365 @@ __global__ void __launch_bounds__(THREADS) k3_smooth(Params P, const T* __restri
     }
 }
 
+// ----------------------------------------------------------------------------
+// Staged variants: the planes a step needs are prefetched into rings of shared
+// memory by asynchronous copies (cp.async, one element per copy, zero-filled
+// outside the grid), issued a few planes ahead of the march, so the loads of
+// plane z+3 are in flight while plane z is computed.  Regions of a plane:
+//   E1 = tile + 1-node ring (34 x 10), origin (x0 - 1, y0 - 1)
+//   E2 = tile + 2-node ring (36 x 12), origin (x0 - 2, y0 - 2)
+//   I  = tile (32 x 8), origin (x0, y0)
+// The floating-point expressions and their order are those of the generic
+// kernels; zero-filled neighbours outside the grid are never read (the same
+// bounds tests decide which faces enter a sum).
+
+constexpr int E2X = TX + 4, E2Y = TY + 4;
+
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// one element global -> shared, asynchronously; zero-filled when !valid (no global read)
+template <typename T>
+__device__ __forceinline__ void cp_elem(T* sdst, const T* gsrc, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sh_addr(sdst)), "l"(gsrc),
+                 "n"((int)sizeof(T)), "r"(valid ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// stage plane zz of vector v (one query) on the RX x RY region with origin (x0, y0) into s
+template <typename T, int RX, int RY>
+__device__ __forceinline__ void stage_plane(T* s, const T* __restrict__ v, const Geo& g, int x0, int y0, int zz) {
+    const long long plane = (long long)g.mx * g.my;
+    const bool zin = zz >= 0 && zz < g.mz;
+    for (int e = threadIdx.x; e < RX * RY; e += THREADS) {
+        const int ix = x0 + e % RX, iy = y0 + e / RX;
+        const bool ok = zin && ix >= 0 && ix < g.mx && iy >= 0 && iy < g.my;
+        cp_elem(s + e, ok ? v + ix + (long long)g.mx * iy + plane * zz : v, ok);
+    }
+}
+
+__host__ __device__ inline int wrap(int k, int n) { return ((k % n) + n) % n; }
+
+// ---- smoother, staged: ring of NSS planes of {src on E2, b on E1, p on E1 (PR only)}
+constexpr int NSS = 5;
+
+template <typename T>
+struct SmoothSmem {
+    T src[NSS][E2Y][E2X];
+    T b[NSS][EY][EX];
+    T pd[NSS][EY][EX];
+    T red[3][EY][EX];
+};
+
+template <typename T, bool LAST>
+__global__ void __launch_bounds__(THREADS) k3s_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmoothSmem<T>& S = *reinterpret_cast<SmoothSmem<T>*>(smem_raw);
+    __shared__ T mus[MAX_MU];
+    __shared__ double red[32];
+    const Geo& g = P.g;
+    const int ntx = (g.mx + TX - 1) / TX, nty = (g.my + TY - 1) / TY;
+    const int ntiles = tiles3(g);
+    const long long plane = (long long)g.mx * g.my;
+    const int cnt = P.lcnt[L_PREC];
+    const long long total = (long long)cnt * ntiles;
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        const int slot = (int)(w / ntiles), tile = (int)(w % ntiles);
+        const int q = P.lidx[L_PREC * P.Bmax + slot];
+        const QState& s = P.st[q];
+        __syncthreads();
+        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
+        const int tx0 = (tile % ntx) * TX;
+        const int ty0 = ((tile / ntx) % nty) * TY;
+        const int z0 = (tile / (ntx * nty)) * ZC;
+        const int z1 = min(z0 + ZC, g.mz);
+        const T* src = src_base + (size_t)q * g.n;
+        T* dst = dst_base + (size_t)q * g.n;
+        const T* b = reinterpret_cast<const T*>(P.r) + (size_t)q * g.n;
+        const bool need_ap = LAST && P.beta_form == RB_BETA_PR && !s.start;
+        const T* pdir = need_ap ? reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * (size_t)g.n : b;
+        auto stage = [&](int k) {
+            const int sl = wrap(k, NSS);
+            if (k <= z1 + 1) {
+                stage_plane<T, E2X, E2Y>(&S.src[sl][0][0], src, g, tx0 - 2, ty0 - 2, k);
+                stage_plane<T, EX, EY>(&S.b[sl][0][0], b, g, tx0 - 1, ty0 - 1, k);
+                if (need_ap) stage_plane<T, EX, EY>(&S.pd[sl][0][0], pdir, g, tx0 - 1, ty0 - 1, k);
+            }
+            cp_commit();
+        };
+        // new red values of plane k on E1 (zero at black points and outside the grid)
+        auto red_plane = [&](int k) {
+            T(*rp)[EX] = S.red[wrap(k, 3)];
+            const T(*sc)[E2X] = S.src[wrap(k, NSS)];
+            const T(*sm)[E2X] = S.src[wrap(k - 1, NSS)];
+            const T(*sp)[E2X] = S.src[wrap(k + 1, NSS)];
+            const T(*bk)[EX] = S.b[wrap(k, NSS)];
+            for (int e = threadIdx.x; e < EX * EY; e += THREADS) {
+                const int ex = e % EX, ey = e / EX;
+                const int ix = tx0 + ex - 1, iy = ty0 + ey - 1;
+                T val = T(0);
+                if (k >= 0 && k < g.mz && ix >= 0 && ix < g.mx && iy >= 0 && iy < g.my && ((ix + iy + k) & 1) == 0) {
+                    Coef<T> c;
+                    node_coef(g, mus, ix, iy, k, c);
+                    T sum = T(0);
+                    if (ix > 0) sum += c.kxm * sc[ey + 1][ex];
+                    if (ix < g.mx - 1) sum += c.kxp * sc[ey + 1][ex + 2];
+                    if (iy > 0) sum += c.kym * sc[ey][ex + 1];
+                    if (iy < g.my - 1) sum += c.kyp * sc[ey + 2][ex + 1];
+                    if (k > 0) sum += c.kzm * sm[ey + 1][ex + 1];
+                    if (k < g.mz - 1) sum += c.kzp * sp[ey + 1][ex + 1];
+                    val = (bk[ey][ex] + sum) / c.diag;
+                }
+                rp[ey][ex] = val;
+            }
+        };
+        for (int k = z0 - 2; k <= z0 + 2; ++k) stage(k);
+        cp_wait<2>();               // planes z0-2 .. z0
+        __syncthreads();
+        red_plane(z0 - 1);
+        cp_wait<1>();               // plane z0+1
+        __syncthreads();
+        red_plane(z0);
+        T ry = T(0), roy = T(0);
+        for (int z = z0; z < z1; ++z) {
+            stage(z + 3);           // into the slot of plane z-2, last read before the previous barrier
+            cp_wait<1>();           // plane z+2
+            __syncthreads();
+            red_plane(z + 1);
+            __syncthreads();
+            const int ix = tx0 + lx, iy = ty0 + ly;
+            if (ix < g.mx && iy < g.my) {
+                const long long i = ix + (long long)g.mx * iy + plane * z;
+                const T(*rc)[EX] = S.red[wrap(z, 3)];
+                const T bi = S.b[wrap(z, NSS)][ly + 1][lx + 1];
+                T v;
+                if (((ix + iy + z) & 1) == 0) {
+                    v = rc[ly + 1][lx + 1];
+                } else {
+                    const T(*rm)[EX] = S.red[wrap(z - 1, 3)];
+                    const T(*rpz)[EX] = S.red[wrap(z + 1, 3)];
+                    Coef<T> c;
+                    node_coef(g, mus, ix, iy, z, c);
+                    T sum = T(0);
+                    if (ix > 0) sum += c.kxm * rc[ly + 1][lx];
+                    if (ix < g.mx - 1) sum += c.kxp * rc[ly + 1][lx + 2];
+                    if (iy > 0) sum += c.kym * rc[ly][lx + 1];
+                    if (iy < g.my - 1) sum += c.kyp * rc[ly + 2][lx + 1];
+                    if (z > 0) sum += c.kzm * rm[ly + 1][lx + 1];
+                    if (z < g.mz - 1) sum += c.kzp * rpz[ly + 1][lx + 1];
+                    v = (bi + sum) / c.diag;
+                }
+                dst[i] = v;
+                if constexpr (LAST) {
+                    ry += bi * v;
+                    if (need_ap) {
+                        const T(*pc)[EX] = S.pd[wrap(z, NSS)];
+                        const T(*pm)[EX] = S.pd[wrap(z - 1, NSS)];
+                        const T(*pp)[EX] = S.pd[wrap(z + 1, NSS)];
+                        Coef<T> c;
+                        node_coef(g, mus, ix, iy, z, c);
+                        T sum = T(0);
+                        if (ix > 0) sum += c.kxm * pc[ly + 1][lx];
+                        if (ix < g.mx - 1) sum += c.kxp * pc[ly + 1][lx + 2];
+                        if (iy > 0) sum += c.kym * pc[ly][lx + 1];
+                        if (iy < g.my - 1) sum += c.kyp * pc[ly + 2][lx + 1];
+                        if (z > 0) sum += c.kzm * pm[ly + 1][lx + 1];
+                        if (z < g.mz - 1) sum += c.kzp * pp[ly + 1][lx + 1];
+                        const T ap = c.diag * pc[ly + 1][lx + 1] - sum;
+                        roy += ap * v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        cp_wait<0>();               // nothing of this item may land in the next one's slots
+        if constexpr (LAST) {
+            double v[2];
+            v[0] = bsum(ry, red);
+            v[1] = bsum(roy, red);
+            if (arrive(P, q, tile, ntiles, v, 2)) {
+                double tot[2];
+                gather_partials(P, q, ntiles, 2, tot, red);
+                if (threadIdx.x == 0) {
+                    finalize_prec_state(P, q, tot[0], tot[1]);
+                    P.tick[q] = 0;
+                }
+            }
+        }
+    }
+}
+
+// ---- CG body, staged: ring of NSC planes on E1 (p or y, p_old) and on I (r, d)
+constexpr int NSC = 4;
+
+template <typename T>
+struct CgSmem {
+    T a[NSC][EY][EX];      // cg_a: y; cg_b: p
+    T c[NSC][EY][EX];      // cg_a: p_old
+    T r[NSC][TY][TX];      // cg_b: r
+    T d[NSC][TY][TX];      // cg_b: d
+};
+
+// part A: p_new = y + beta p_old on the tile, p_new^T A p_new (Alg. 3 steps 11, 5);
+// part B: d += alpha p, r -= alpha A p, ||r||^2 (steps 6-8)
+template <typename T, bool PART_A>
+__global__ void __launch_bounds__(THREADS) k3s_cg(Params P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CgSmem<T>& S = *reinterpret_cast<CgSmem<T>*>(smem_raw);
+    __shared__ T mus[MAX_MU];
+    __shared__ double red[32];
+    const Geo& g = P.g;
+    const int ntx = (g.mx + TX - 1) / TX, nty = (g.my + TY - 1) / TY;
+    const int ntiles = tiles3(g);
+    const long long plane = (long long)g.mx * g.my;
+    const int cnt = P.lcnt[L_ITER];
+    const long long total = (long long)cnt * ntiles;
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        const int slot = (int)(w / ntiles), tile = (int)(w % ntiles);
+        const int q = P.lidx[L_ITER * P.Bmax + slot];
+        const QState& s = P.st[q];
+        if (s.phase != PH_ITER) continue;          // uniform across the CTA
+        __syncthreads();
+        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
+        const int tx0 = (tile % ntx) * TX;
+        const int ty0 = ((tile / ntx) % nty) * TY;
+        const int z0 = (tile / (ntx * nty)) * ZC;
+        const int z1 = min(z0 + ZC, g.mz);
+        const T beta = (T)s.beta;
+        const T alpha = (T)s.alpha;
+        const bool use_old = PART_A && beta != T(0);
+        const size_t qn = (size_t)q * g.n;
+        const T* va = PART_A ? reinterpret_cast<const T*>(P.y) + qn
+                             : reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * (size_t)g.n;
+        const T* vc = reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * (size_t)g.n;   // p_old (A)
+        T* pnew = reinterpret_cast<T*>(P.p) + ((size_t)q * 2 + (s.ppar ^ 1)) * (size_t)g.n;
+        T* rr = reinterpret_cast<T*>(P.r) + qn;
+        T* dd = P.mixed ? reinterpret_cast<T*>(P.d) + qn : reinterpret_cast<T*>(P.x64 + qn);
+        auto stage = [&](int k) {
+            const int sl = wrap(k, NSC);
+            if (k <= z1) {
+                stage_plane<T, EX, EY>(&S.a[sl][0][0], va, g, tx0 - 1, ty0 - 1, k);
+                if (use_old) stage_plane<T, EX, EY>(&S.c[sl][0][0], vc, g, tx0 - 1, ty0 - 1, k);
+                if (!PART_A && k >= z0 && k < z1) {
+                    stage_plane<T, TX, TY>(&S.r[sl][0][0], rr, g, tx0, ty0, k);
+                    stage_plane<T, TX, TY>(&S.d[sl][0][0], dd, g, tx0, ty0, k);
+                }
+            }
+            cp_commit();
+        };
+        // the operand of the stencil at E1 position (ex, ey) of plane k
+        auto opv = [&](int k, int ex, int ey) -> T {
+            const int sl = wrap(k, NSC);
+            if (PART_A) return use_old ? S.a[sl][ey][ex] + beta * S.c[sl][ey][ex] : S.a[sl][ey][ex];
+            return S.a[sl][ey][ex];
+        };
+        for (int k = z0 - 1; k <= z0 + 1; ++k) stage(k);
+        T acc = T(0);
+        for (int z = z0; z < z1; ++z) {
+            stage(z + 2);           // into the slot of plane z-2, last read before the previous barrier
+            cp_wait<1>();           // planes up to z+1
+            __syncthreads();
+            const int ix = tx0 + lx, iy = ty0 + ly;
+            if (ix < g.mx && iy < g.my) {
+                const long long i = ix + (long long)g.mx * iy + plane * z;
+                Coef<T> c;
+                node_coef(g, mus, ix, iy, z, c);
+                const T pi = opv(z, lx + 1, ly + 1);
+                T sum = T(0);
+                if (ix > 0) sum += c.kxm * opv(z, lx, ly + 1);
+                if (ix < g.mx - 1) sum += c.kxp * opv(z, lx + 2, ly + 1);
+                if (iy > 0) sum += c.kym * opv(z, lx + 1, ly);
+                if (iy < g.my - 1) sum += c.kyp * opv(z, lx + 1, ly + 2);
+                if (z > 0) sum += c.kzm * opv(z - 1, lx + 1, ly + 1);
+                if (z < g.mz - 1) sum += c.kzp * opv(z + 1, lx + 1, ly + 1);
+                const T api = c.diag * pi - sum;
+                if constexpr (PART_A) {
+                    pnew[i] = pi;
+                    acc += pi * api;
+                } else {
+                    const int sl = wrap(z, NSC);
+                    dd[i] = S.d[sl][ly][lx] + alpha * pi;
+                    const T rv = S.r[sl][ly][lx] - alpha * api;
+                    rr[i] = rv;
+                    acc += rv * rv;
+                }
+            }
+            __syncthreads();
+        }
+        cp_wait<0>();
+        double v = bsum(acc, red);
+        if (arrive(P, q, tile, ntiles, &v, 1)) {
+            double tot;
+            gather_partials(P, q, ntiles, 1, &tot, red);
+            if (threadIdx.x == 0) {
+                if constexpr (PART_A) finalize_cg_a_state(P, q, tot);
+                else finalize_cg_b_state(P, q, tot);
+                P.tick[q] = 0;
+            }
+        }
+    }
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 }  // namespace
 
 bool use_zmarch_smoother(const Geo& g) { return g.dim == 3 && tiles3(g) <= tiles_flat(g.n); }
+
+template <typename T>
+void launch3d_smooth_staged(const Params& P, const Launch& L, int nu) {
+    static bool configured = false;
+    const size_t sm = sizeof(SmoothSmem<T>);
+    if (!configured) {
+        allow_smem(k3s_smooth<T, true>, sm);
+        allow_smem(k3s_smooth<T, false>, sm);
+        configured = true;
+    }
+    T* ypro = reinterpret_cast<T*>(P.ypro);
+    T* tmp = reinterpret_cast<T*>(P.tmp);
+    T* out = reinterpret_cast<T*>(P.y);
+    const int sweeps = nu < 1 ? 1 : nu;
+    const T* src = ypro;
+    for (int s = 1; s <= sweeps; ++s) {
+        const bool last = s == sweeps;
+        T* dst = last ? out : ((s & 1) ? tmp : ypro);
+        if (last) k3s_smooth<T, true><<<L.grid, THREADS, sm, L.s>>>(P, src, dst);
+        else k3s_smooth<T, false><<<L.grid, THREADS, sm, L.s>>>(P, src, dst);
+        src = dst;
+    }
+}
+template void launch3d_smooth_staged<float>(const Params&, const Launch&, int);
+template void launch3d_smooth_staged<double>(const Params&, const Launch&, int);
+
+template <typename T>
+void launch3d_cg_a(const Params& P, const Launch& L) {
+    static bool configured = false;
+    if (!configured) {
+        allow_smem(k3s_cg<T, true>, sizeof(CgSmem<T>));
+        configured = true;
+    }
+    k3s_cg<T, true><<<L.grid, THREADS, sizeof(CgSmem<T>), L.s>>>(P);
+}
+template <typename T>
+void launch3d_cg_b(const Params& P, const Launch& L) {
+    static bool configured = false;
+    if (!configured) {
+        allow_smem(k3s_cg<T, false>, sizeof(CgSmem<T>));
+        configured = true;
+    }
+    k3s_cg<T, false><<<L.grid, THREADS, sizeof(CgSmem<T>), L.s>>>(P);
+}
+template void launch3d_cg_a<float>(const Params&, const Launch&);
+template void launch3d_cg_a<double>(const Params&, const Launch&);
+template void launch3d_cg_b<float>(const Params&, const Launch&);
+template void launch3d_cg_b<double>(const Params&, const Launch&);
 
 // nu sweeps ypro -> tmp -> ypro ... -> y, as the generic smoother
 template <typename T>
