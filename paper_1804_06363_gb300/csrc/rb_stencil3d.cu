@@ -174,22 +174,73 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// stage plane zz of vector v (one query) on the RX x RY region with origin (x0, y0) into s
-template <typename T, int RX, int RY>
-__device__ __forceinline__ void stage_plane(T* s, const T* __restrict__ v, const Geo& g, int x0, int y0, int zz) {
-    const long long plane = (long long)g.mx * g.my;
-    const bool zin = zz >= 0 && zz < g.mz;
-    for (int e = threadIdx.x; e < RX * RY; e += THREADS) {
-        const int ix = x0 + e % RX, iy = y0 + e / RX;
-        const bool ok = zin && ix >= 0 && ix < g.mx && iy >= 0 && iy < g.my;
-        cp_elem(s + e, ok ? v + ix + (long long)g.mx * iy + plane * zz : v, ok);
+// Per-thread plan for staging one RX x RY region: the in-plane offsets of the
+// thread's elements and which of them lie in the grid (computed once per work
+// item; a plane then costs one address and one copy per element).
+template <int RX, int RY>
+struct StagePlan {
+    static constexpr int MAXE = (RX * RY + THREADS - 1) / THREADS;
+    int off[MAXE];
+    unsigned ok;
+    __device__ __forceinline__ void init(const Geo& g, int x0, int y0) {
+        ok = 0u;
+#pragma unroll
+        for (int j = 0; j < MAXE; ++j) {
+            const int e = threadIdx.x + j * THREADS;
+            off[j] = 0;
+            const int ix = x0 + e % RX, iy = y0 + e / RX;
+            if (e < RX * RY && ix >= 0 && ix < g.mx && iy >= 0 && iy < g.my) {
+                off[j] = ix + g.mx * iy;
+                ok |= 1u << j;
+            }
+        }
     }
-}
+    // plane zz of v into s (zero outside the grid)
+    template <typename T>
+    __device__ __forceinline__ void stage(T* s, const T* __restrict__ v, const Geo& g, int zz) const {
+        const bool zin = zz >= 0 && zz < g.mz;
+        const T* vp = v + (long long)g.mx * g.my * (zin ? zz : 0);
+#pragma unroll
+        for (int j = 0; j < MAXE; ++j) {
+            const int e = threadIdx.x + j * THREADS;
+            if (e < RX * RY) {
+                const bool valid = zin && ((ok >> j) & 1u);
+                cp_elem(s + e, valid ? vp + off[j] : v, valid);
+            }
+        }
+    }
+};
 
 __host__ __device__ inline int wrap(int k, int n) { return ((k % n) + n) % n; }
 
+// Key of the z-dependence of a node's face coefficients: the blocks of planes
+// k-1, k, k+1 (0xFF where the face lies on the boundary).  Equal keys at the
+// same (x, y) give equal coefficients, so a thread rebuilds its Coef only when
+// the key changes (at block boundaries in z).
+constexpr int ZK = ZC + 4;   // planes z0-2 .. z0+ZC+1
+__device__ __forceinline__ void fill_zkeys(int* zk, const Geo& g, int z0) {
+    for (int t = threadIdx.x; t < ZK; t += THREADS) {
+        const int k = z0 - 2 + t;
+        int key = -1;
+        if (k >= 0 && k < g.mz)
+            key = ((k > 0 ? __ldg(g.bz + k - 1) : 0xFF) << 16) | (__ldg(g.bz + k) << 8) |
+                  (k < g.mz - 1 ? __ldg(g.bz + k + 1) : 0xFF);
+        zk[t] = key;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void cached_coef(const Geo& g, const T* mus, int ix, int iy, int k, int key, Coef<T>& c,
+                                            int& ckey) {
+    if (ckey != key) {
+        node_coef(g, mus, ix, iy, k, c);
+        ckey = key;
+    }
+}
+
 // ---- smoother, staged: ring of NSS planes of {src on E2, b on E1, p on E1 (PR only)}
 constexpr int NSS = 5;
+constexpr int RED_PTS = EY * (EX / 2);   // red points of an E1 plane (EX even)
 
 template <typename T>
 struct SmoothSmem {
@@ -200,10 +251,11 @@ struct SmoothSmem {
 };
 
 template <typename T, bool LAST>
-__global__ void __launch_bounds__(THREADS) k3s_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
+__global__ void __launch_bounds__(THREADS, 3) k3s_smooth(Params P, const T* __restrict__ src_base, T* dst_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmoothSmem<T>& S = *reinterpret_cast<SmoothSmem<T>*>(smem_raw);
     __shared__ T mus[MAX_MU];
+    __shared__ int zk[ZK];
     __shared__ double red[32];
     const Geo& g = P.g;
     const int ntx = (g.mx + TX - 1) / TX, nty = (g.my + TY - 1) / TY;
@@ -212,91 +264,105 @@ __global__ void __launch_bounds__(THREADS) k3s_smooth(Params P, const T* __restr
     const int cnt = P.lcnt[L_PREC];
     const long long total = (long long)cnt * ntiles;
     const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+    // this thread's red point of an E1 plane: row rey, x = 2 rj + parity
+    const int rey = threadIdx.x / (EX / 2), rj = threadIdx.x % (EX / 2);
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / ntiles), tile = (int)(w % ntiles);
         const int q = P.lidx[L_PREC * P.Bmax + slot];
         const QState& s = P.st[q];
-        __syncthreads();
-        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
         const int tx0 = (tile % ntx) * TX;
         const int ty0 = ((tile / ntx) % nty) * TY;
         const int z0 = (tile / (ntx * nty)) * ZC;
         const int z1 = min(z0 + ZC, g.mz);
+        __syncthreads();
+        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
+        fill_zkeys(zk, g, z0);
         const T* src = src_base + (size_t)q * g.n;
         T* dst = dst_base + (size_t)q * g.n;
         const T* b = reinterpret_cast<const T*>(P.r) + (size_t)q * g.n;
         const bool need_ap = LAST && P.beta_form == RB_BETA_PR && !s.start;
         const T* pdir = need_ap ? reinterpret_cast<const T*>(P.p) + ((size_t)q * 2 + s.ppar) * (size_t)g.n : b;
+        StagePlan<E2X, E2Y> p2;
+        StagePlan<EX, EY> p1;
+        p2.init(g, tx0 - 2, ty0 - 2);
+        p1.init(g, tx0 - 1, ty0 - 1);
         auto stage = [&](int k) {
             const int sl = wrap(k, NSS);
             if (k <= z1 + 1) {
-                stage_plane<T, E2X, E2Y>(&S.src[sl][0][0], src, g, tx0 - 2, ty0 - 2, k);
-                stage_plane<T, EX, EY>(&S.b[sl][0][0], b, g, tx0 - 1, ty0 - 1, k);
-                if (need_ap) stage_plane<T, EX, EY>(&S.pd[sl][0][0], pdir, g, tx0 - 1, ty0 - 1, k);
+                p2.stage(&S.src[sl][0][0], src, g, k);
+                p1.stage(&S.b[sl][0][0], b, g, k);
+                if (need_ap) p1.stage(&S.pd[sl][0][0], pdir, g, k);
             }
             cp_commit();
         };
-        // new red values of plane k on E1 (zero at black points and outside the grid)
+        // coefficient caches: the red point of even / odd planes, the tile point
+        Coef<T> cr0, cr1, ci;
+        int kr0 = -1, kr1 = -1, ki = -1;
+        // new red values of plane k on E1; black entries and points outside the grid are
+        // never read, so only the RED_PTS red points are computed (one per thread)
         auto red_plane = [&](int k) {
-            T(*rp)[EX] = S.red[wrap(k, 3)];
+            if (k < 0 || k >= g.mz || threadIdx.x >= RED_PTS) return;
+            const int iy = ty0 - 1 + rey;
+            const int ex = 2 * rj + ((1 + tx0 + iy + k) & 1);
+            const int ix = tx0 - 1 + ex;
+            if (ix < 0 || ix >= g.mx || iy < 0 || iy >= g.my) return;
+            const int key = zk[k - z0 + 2];
+            Coef<T> c;
+            if (k & 1) {
+                cached_coef(g, mus, ix, iy, k, key, cr1, kr1);
+                c = cr1;
+            } else {
+                cached_coef(g, mus, ix, iy, k, key, cr0, kr0);
+                c = cr0;
+            }
             const T(*sc)[E2X] = S.src[wrap(k, NSS)];
             const T(*sm)[E2X] = S.src[wrap(k - 1, NSS)];
             const T(*sp)[E2X] = S.src[wrap(k + 1, NSS)];
-            const T(*bk)[EX] = S.b[wrap(k, NSS)];
-            for (int e = threadIdx.x; e < EX * EY; e += THREADS) {
-                const int ex = e % EX, ey = e / EX;
-                const int ix = tx0 + ex - 1, iy = ty0 + ey - 1;
-                T val = T(0);
-                if (k >= 0 && k < g.mz && ix >= 0 && ix < g.mx && iy >= 0 && iy < g.my && ((ix + iy + k) & 1) == 0) {
-                    Coef<T> c;
-                    node_coef(g, mus, ix, iy, k, c);
-                    T sum = T(0);
-                    if (ix > 0) sum += c.kxm * sc[ey + 1][ex];
-                    if (ix < g.mx - 1) sum += c.kxp * sc[ey + 1][ex + 2];
-                    if (iy > 0) sum += c.kym * sc[ey][ex + 1];
-                    if (iy < g.my - 1) sum += c.kyp * sc[ey + 2][ex + 1];
-                    if (k > 0) sum += c.kzm * sm[ey + 1][ex + 1];
-                    if (k < g.mz - 1) sum += c.kzp * sp[ey + 1][ex + 1];
-                    val = (bk[ey][ex] + sum) / c.diag;
-                }
-                rp[ey][ex] = val;
-            }
+            T sum = T(0);
+            if (ix > 0) sum += c.kxm * sc[rey + 1][ex];
+            if (ix < g.mx - 1) sum += c.kxp * sc[rey + 1][ex + 2];
+            if (iy > 0) sum += c.kym * sc[rey][ex + 1];
+            if (iy < g.my - 1) sum += c.kyp * sc[rey + 2][ex + 1];
+            if (k > 0) sum += c.kzm * sm[rey + 1][ex + 1];
+            if (k < g.mz - 1) sum += c.kzp * sp[rey + 1][ex + 1];
+            S.red[wrap(k, 3)][rey][ex] = (S.b[wrap(k, NSS)][rey][ex] + sum) / c.diag;
         };
         for (int k = z0 - 2; k <= z0 + 2; ++k) stage(k);
-        cp_wait<2>();               // planes z0-2 .. z0
+        cp_wait<2>();               // planes z0-2 .. z0 (and mus, zk)
         __syncthreads();
         red_plane(z0 - 1);
         cp_wait<1>();               // plane z0+1
         __syncthreads();
         red_plane(z0);
         T ry = T(0), roy = T(0);
+        const int ix = tx0 + lx, iy = ty0 + ly;
+        const bool inside = ix < g.mx && iy < g.my;
         for (int z = z0; z < z1; ++z) {
             stage(z + 3);           // into the slot of plane z-2, last read before the previous barrier
             cp_wait<1>();           // plane z+2
             __syncthreads();
             red_plane(z + 1);
             __syncthreads();
-            const int ix = tx0 + lx, iy = ty0 + ly;
-            if (ix < g.mx && iy < g.my) {
+            if (inside) {
                 const long long i = ix + (long long)g.mx * iy + plane * z;
                 const T(*rc)[EX] = S.red[wrap(z, 3)];
                 const T bi = S.b[wrap(z, NSS)][ly + 1][lx + 1];
+                const bool is_red = ((ix + iy + z) & 1) == 0;
+                if (!is_red || need_ap) cached_coef(g, mus, ix, iy, z, zk[z - z0 + 2], ci, ki);
                 T v;
-                if (((ix + iy + z) & 1) == 0) {
+                if (is_red) {
                     v = rc[ly + 1][lx + 1];
                 } else {
                     const T(*rm)[EX] = S.red[wrap(z - 1, 3)];
                     const T(*rpz)[EX] = S.red[wrap(z + 1, 3)];
-                    Coef<T> c;
-                    node_coef(g, mus, ix, iy, z, c);
                     T sum = T(0);
-                    if (ix > 0) sum += c.kxm * rc[ly + 1][lx];
-                    if (ix < g.mx - 1) sum += c.kxp * rc[ly + 1][lx + 2];
-                    if (iy > 0) sum += c.kym * rc[ly][lx + 1];
-                    if (iy < g.my - 1) sum += c.kyp * rc[ly + 2][lx + 1];
-                    if (z > 0) sum += c.kzm * rm[ly + 1][lx + 1];
-                    if (z < g.mz - 1) sum += c.kzp * rpz[ly + 1][lx + 1];
-                    v = (bi + sum) / c.diag;
+                    if (ix > 0) sum += ci.kxm * rc[ly + 1][lx];
+                    if (ix < g.mx - 1) sum += ci.kxp * rc[ly + 1][lx + 2];
+                    if (iy > 0) sum += ci.kym * rc[ly][lx + 1];
+                    if (iy < g.my - 1) sum += ci.kyp * rc[ly + 2][lx + 1];
+                    if (z > 0) sum += ci.kzm * rm[ly + 1][lx + 1];
+                    if (z < g.mz - 1) sum += ci.kzp * rpz[ly + 1][lx + 1];
+                    v = (bi + sum) / ci.diag;
                 }
                 dst[i] = v;
                 if constexpr (LAST) {
@@ -305,16 +371,14 @@ __global__ void __launch_bounds__(THREADS) k3s_smooth(Params P, const T* __restr
                         const T(*pc)[EX] = S.pd[wrap(z, NSS)];
                         const T(*pm)[EX] = S.pd[wrap(z - 1, NSS)];
                         const T(*pp)[EX] = S.pd[wrap(z + 1, NSS)];
-                        Coef<T> c;
-                        node_coef(g, mus, ix, iy, z, c);
                         T sum = T(0);
-                        if (ix > 0) sum += c.kxm * pc[ly + 1][lx];
-                        if (ix < g.mx - 1) sum += c.kxp * pc[ly + 1][lx + 2];
-                        if (iy > 0) sum += c.kym * pc[ly][lx + 1];
-                        if (iy < g.my - 1) sum += c.kyp * pc[ly + 2][lx + 1];
-                        if (z > 0) sum += c.kzm * pm[ly + 1][lx + 1];
-                        if (z < g.mz - 1) sum += c.kzp * pp[ly + 1][lx + 1];
-                        const T ap = c.diag * pc[ly + 1][lx + 1] - sum;
+                        if (ix > 0) sum += ci.kxm * pc[ly + 1][lx];
+                        if (ix < g.mx - 1) sum += ci.kxp * pc[ly + 1][lx + 2];
+                        if (iy > 0) sum += ci.kym * pc[ly][lx + 1];
+                        if (iy < g.my - 1) sum += ci.kyp * pc[ly + 2][lx + 1];
+                        if (z > 0) sum += ci.kzm * pm[ly + 1][lx + 1];
+                        if (z < g.mz - 1) sum += ci.kzp * pp[ly + 1][lx + 1];
+                        const T ap = ci.diag * pc[ly + 1][lx + 1] - sum;
                         roy += ap * v;
                     }
                 }
@@ -356,6 +420,7 @@ __global__ void __launch_bounds__(THREADS) k3s_cg(Params P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CgSmem<T>& S = *reinterpret_cast<CgSmem<T>*>(smem_raw);
     __shared__ T mus[MAX_MU];
+    __shared__ int zk[ZK];
     __shared__ double red[32];
     const Geo& g = P.g;
     const int ntx = (g.mx + TX - 1) / TX, nty = (g.my + TY - 1) / TY;
@@ -369,12 +434,13 @@ __global__ void __launch_bounds__(THREADS) k3s_cg(Params P) {
         const int q = P.lidx[L_ITER * P.Bmax + slot];
         const QState& s = P.st[q];
         if (s.phase != PH_ITER) continue;          // uniform across the CTA
-        __syncthreads();
-        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
         const int tx0 = (tile % ntx) * TX;
         const int ty0 = ((tile / ntx) % nty) * TY;
         const int z0 = (tile / (ntx * nty)) * ZC;
         const int z1 = min(z0 + ZC, g.mz);
+        __syncthreads();
+        if (threadIdx.x < P.n_mu) mus[threadIdx.x] = (T)P.mu[(size_t)q * P.n_mu + threadIdx.x];
+        fill_zkeys(zk, g, z0);
         const T beta = (T)s.beta;
         const T alpha = (T)s.alpha;
         const bool use_old = PART_A && beta != T(0);
@@ -385,14 +451,18 @@ __global__ void __launch_bounds__(THREADS) k3s_cg(Params P) {
         T* pnew = reinterpret_cast<T*>(P.p) + ((size_t)q * 2 + (s.ppar ^ 1)) * (size_t)g.n;
         T* rr = reinterpret_cast<T*>(P.r) + qn;
         T* dd = P.mixed ? reinterpret_cast<T*>(P.d) + qn : reinterpret_cast<T*>(P.x64 + qn);
+        StagePlan<EX, EY> p1;
+        StagePlan<TX, TY> p0;
+        p1.init(g, tx0 - 1, ty0 - 1);
+        if (!PART_A) p0.init(g, tx0, ty0);
         auto stage = [&](int k) {
             const int sl = wrap(k, NSC);
             if (k <= z1) {
-                stage_plane<T, EX, EY>(&S.a[sl][0][0], va, g, tx0 - 1, ty0 - 1, k);
-                if (use_old) stage_plane<T, EX, EY>(&S.c[sl][0][0], vc, g, tx0 - 1, ty0 - 1, k);
+                p1.stage(&S.a[sl][0][0], va, g, k);
+                if (use_old) p1.stage(&S.c[sl][0][0], vc, g, k);
                 if (!PART_A && k >= z0 && k < z1) {
-                    stage_plane<T, TX, TY>(&S.r[sl][0][0], rr, g, tx0, ty0, k);
-                    stage_plane<T, TX, TY>(&S.d[sl][0][0], dd, g, tx0, ty0, k);
+                    p0.stage(&S.r[sl][0][0], rr, g, k);
+                    p0.stage(&S.d[sl][0][0], dd, g, k);
                 }
             }
             cp_commit();
@@ -404,16 +474,18 @@ __global__ void __launch_bounds__(THREADS) k3s_cg(Params P) {
             return S.a[sl][ey][ex];
         };
         for (int k = z0 - 1; k <= z0 + 1; ++k) stage(k);
+        Coef<T> c;
+        int ckey = -1;
         T acc = T(0);
+        const int ix = tx0 + lx, iy = ty0 + ly;
+        const bool inside = ix < g.mx && iy < g.my;
         for (int z = z0; z < z1; ++z) {
             stage(z + 2);           // into the slot of plane z-2, last read before the previous barrier
-            cp_wait<1>();           // planes up to z+1
+            cp_wait<1>();           // planes up to z+1 (and mus, zk)
             __syncthreads();
-            const int ix = tx0 + lx, iy = ty0 + ly;
-            if (ix < g.mx && iy < g.my) {
+            if (inside) {
                 const long long i = ix + (long long)g.mx * iy + plane * z;
-                Coef<T> c;
-                node_coef(g, mus, ix, iy, z, c);
+                cached_coef(g, mus, ix, iy, z, zk[z - z0 + 2], c, ckey);
                 const T pi = opv(z, lx + 1, ly + 1);
                 T sum = T(0);
                 if (ix > 0) sum += c.kxm * opv(z, lx, ly + 1);
