@@ -7,6 +7,9 @@ inner RBCG with RBI preconditioner, tensor-core projections), inputs resident
 in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+After the timed region the default run also compares three starts of the same
+solves on rank 0 (cold, Galerkin, learned network; "warm_start" in the JSON).
 """
 from __future__ import annotations
 
@@ -64,7 +67,8 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no per-kernel pass, e2e, FP64 comparator or CPU baseline); for profilers")
     ap.add_argument("--warm", action="store_true",
-                    help="also run the learned warm-start comparison (cold / Galerkin / network start)")
+                    help="run the learned warm-start comparison (cold / Galerkin / network start) also with --quick")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--warm-pairs", type=int, default=4096, help="training pairs (truth solves) of the network")
     ap.add_argument("--warm-steps", type=int, default=2000, help="Adam steps of the network")
     ap.add_argument("--warm-test", type=int, default=0, help="test queries of the comparison (default: the step's)")
@@ -356,7 +360,13 @@ def main():
     progress(f"timed steps: {value:.1f} solves/s, mean iterations {float(last['iters'].mean()):.1f}")
     ok = bool(np.all(last["status"] == rb.RB_OK))
 
-    warm = warm_start_experiment(ctx, w, args, opts, dev, stream) if args.warm and rank == 0 else None
+    # learned warm start (after the timed region; rank 0): on by default, off under --quick unless --warm
+    warm = None
+    if (args.warm or not args.quick) and not args.no_warm and rank == 0:
+        try:
+            warm = warm_start_experiment(ctx, w, args, opts, dev, stream)
+        except Exception as e:  # the comparison must not sink the headline number
+            warm = {"error": f"{type(e).__name__}: {e}"}
 
     if args.quick:
         if rank == 0:
