@@ -266,7 +266,7 @@ rb_status rb_coefficients(rb_ctx* ctx, int B, const double* x, double* coef, voi
 /*
  * Learned warm start: a network c(mu) predicting reduced coefficients (the
  * paper has no learned component; the network only supplies x_0 = W c(mu) to
- * rb_warm_start, and the RB iterations remain the judge of its error).
+ * rb_warm_start; the RB iterations then remove whatever error the prediction has).
  *   features   log mu_i for i < n_log (diffusion coefficients), mu_i for
  *              n_log <= i < n_in (load parameters), standardised by the
  *              per-column mean and population standard deviation (floored at
