@@ -500,9 +500,13 @@ rb_status rb_mlp_create(rb_mlp** out, int n_in, int n_log, int hidden, int n_out
     if (n_in < 1 || n_in > MAX_IN || n_log < 0 || n_log > n_in || hidden < 1 || hidden > MAX_H || n_out < 1 ||
         n_out > MAX_OUT || !params || max_samples < 1)
         return fail(RB_EINVAL, "network sizes out of range (n_in <= 32, hidden <= 128, n_out <= 128) or NULL params");
+    const long long np = (long long)hidden * n_in + hidden + (long long)hidden * hidden + hidden +
+                         (long long)n_out * hidden + n_out;
+    for (long long p = 0; p < np; ++p)
+        if (!std::isfinite(params[p])) return fail(RB_EINVAL, "initial parameters must be finite");
     rb_mlp* n = new rb_mlp();
     n->I = n_in; n->P = n_log; n->H = hidden; n->O = n_out; n->Smax = max_samples;
-    n->np = (long long)hidden * n_in + hidden + (long long)hidden * hidden + hidden + (long long)n_out * hidden + n_out;
+    n->np = np;
     n->tiles_max = (max_samples + TS - 1) / TS;
     n->smem = layout(n_in, hidden, n_out).total;
     rb_status st = RB_OK;
@@ -522,10 +526,7 @@ rb_status rb_mlp_create(rb_mlp** out, int n_in, int n_log, int hidden, int n_out
             malloc_into(n, &n->d_out, (size_t)max_samples * n_out))
             return RB_ENOMEM;
         std::vector<float> w32(n->np);
-        for (long long p = 0; p < n->np; ++p) {
-            if (!std::isfinite(params[p])) return fail(RB_EINVAL, "initial parameters must be finite");
-            w32[p] = (float)params[p];
-        }
+        for (long long p = 0; p < n->np; ++p) w32[p] = (float)params[p];
         MCK(cudaMemcpy(n->d_w, w32.data(), n->np * sizeof(float), cudaMemcpyHostToDevice));
         MCK(cudaMemset(n->d_m, 0, n->np * sizeof(float)));
         MCK(cudaMemset(n->d_v, 0, n->np * sizeof(float)));

@@ -80,6 +80,10 @@ def test_network_and_warm_start_arguments_are_validated_without_gpu(libpath):
         st = lib.rb_mlp_create(ctypes.byref(h), *args, params, 16)
         assert st == rb.RB_EINVAL and not h.value, args
     assert b"sizes" in lib.rb_last_error(None)
+    bad = (ctypes.c_double * (8 * 4 + 8 + 8 * 8 + 8 + 3 * 8 + 3))()
+    bad[5] = float("nan")
+    assert lib.rb_mlp_create(ctypes.byref(h), 4, 2, 8, 3, bad, 16) == rb.RB_EINVAL and not h.value
+    assert b"finite" in lib.rb_last_error(None)
     assert lib.rb_mlp_num_params(None) == -1
     assert lib.rb_warm_start(None, None, 1, None, None, None, None) == rb.RB_EINVAL
     assert lib.rb_coefficients(None, 1, None, None, None) == rb.RB_EINVAL
