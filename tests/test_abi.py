@@ -88,3 +88,21 @@ def test_network_and_warm_start_arguments_are_validated_without_gpu(libpath):
     assert lib.rb_warm_start(None, None, 1, None, None, None, None) == rb.RB_EINVAL
     assert lib.rb_coefficients(None, 1, None, None, None) == rb.RB_EINVAL
     lib.rb_mlp_free(None)
+
+
+def test_network_parameter_layout_round_trip():
+    """flatten_params follows the header's order (W1, b1, W2, b2, W3, b3) and unflatten_params inverts it."""
+    import numpy as np
+
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+    sizes = (5, 7, 7, 3)
+    layers = [(W, np.arange(W.shape[0], dtype=float) + 100 * l) for l, (W, _) in enumerate(wl.mlp_init(sizes))]
+    flat = rb.flatten_params(layers)
+    assert flat.size == 5 * 7 + 7 + 7 * 7 + 7 + 7 * 3 + 3
+    np.testing.assert_array_equal(flat[:35], layers[0][0].ravel())
+    np.testing.assert_array_equal(flat[35:42], layers[0][1])
+    back = rb.unflatten_params(flat, sizes)
+    for (W, b), (W2, b2) in zip(layers, back):
+        np.testing.assert_array_equal(W, W2)
+        np.testing.assert_array_equal(b, b2)
