@@ -10,8 +10,16 @@ Readings of the paper (where it is silent or loose):
     (the relative residual of eq. relerr); it is applied to the recurrence
     residual, and at exit the true residual f - A x is recomputed: if it is
     not below tol either, the residual is replaced by the true one and the
-    iteration restarts from the current x (counted in the same budget),
-    aiming at tol/2 so that the next true residual clears tol;
+    iteration restarts from the current x (counted in the same budget) with
+    the same stopping test.  `restart_factor` < 1 makes the restarted cycles
+    aim at restart_factor * tol instead (a solver policy, not the paper's);
+  * the adaptive choice of N at the end of Section 4.1: when the residual
+    falls by less than a factor gamma in one iteration,
+    ||r_k|| / ||r_{k+1}|| < gamma, the next preconditioner application uses
+    one more basis vector (N <- N + 1, at most the basis size).  W_N is nested
+    in W_{N+1}, so the reduced matrix of size N is the leading block of the
+    full A_N(mu); the starting N is not given in the paper (argument
+    `adaptive_n`, off when 0);
   * Alg. 3 step 1 writes A without mu; it is A(mu).  With x_0 = 0 the first
     residual is f itself, so no matrix-vector product is spent on it;
   * RBI(A, r, W, 1) inside Alg. 3 starts from x = 0, so its own residual is r:
@@ -121,6 +129,7 @@ class SolveResult:
     converged: bool
     history: List[float]           # relative residual after each iteration
     restarts: int = 0
+    n_history: Optional[List[int]] = None   # RBCG: basis size N of each preconditioner application
 
 
 def rbi(basis: Basis, mu, tol=1e-10, max_iter=1000, smoother="rbgs", nu=1,
@@ -146,9 +155,23 @@ def rbi(basis: Basis, mu, tol=1e-10, max_iter=1000, smoother="rbgs", nu=1,
         it += 1
 
 
+def leading_factor(basis: Basis, mu, k: int):
+    """Cholesky factor of the leading k x k block of A_N(mu): the reduced matrix of the
+    nested basis W_k (the first k columns of W)."""
+    A_N, _ = reduced_system(basis, mu)
+    return sla.cho_factor(A_N[:k, :k], lower=True)
+
+
 def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
-         omega=2.0 / 3.0, beta="fr", x0=None, b=None, apply_counter=None) -> SolveResult:
-    """Alg. 3, with the readings listed in the module docstring."""
+         omega=2.0 / 3.0, beta="fr", x0=None, b=None, apply_counter=None,
+         restart_factor=1.0, adaptive_n=0, gamma=10.0) -> SolveResult:
+    """Alg. 3, with the readings listed in the module docstring.
+
+    adaptive_n = 0 uses the whole basis in every preconditioner application;
+    adaptive_n = k >= 1 starts with W_k and grows N by one after every
+    iteration whose residual ratio ||r_k|| / ||r_{k+1}|| is below gamma (end of
+    Section 4.1).  The N of each application is recorded in `n_history`.
+    """
     prob = basis.prob
     b = pb.load(prob, mu) if b is None else np.asarray(b, dtype=np.float64)
     bn = np.linalg.norm(b)
@@ -158,8 +181,19 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
             apply_counter[0] += 1
         return pb.apply(prob, mu, v)
 
-    factor = reduced_factor(basis, mu) if basis.N > 0 else None
-    Minv = lambda r: rbi_precondition(basis, mu, factor, r, smoother, nu, omega)
+    n_cur = basis.N if adaptive_n <= 0 else min(adaptive_n, basis.N)
+    nested = {}
+
+    def Minv(r):
+        """RBI(A, r, W_N, 1) with the current N (the nested basis W_N = first N columns)."""
+        n_hist.append(n_cur)
+        if n_cur not in nested:
+            sub = basis if n_cur == basis.N else basis.truncated(n_cur)
+            nested[n_cur] = (sub, reduced_factor(sub, mu) if n_cur > 0 else None)
+        sub, factor = nested[n_cur]
+        return rbi_precondition(sub, mu, factor, r, smoother, nu, omega)
+
+    n_hist: List[int] = []
     if x0 is None:
         x = np.zeros(prob.n_dof)
         r = b.copy()
@@ -183,6 +217,8 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
             hist.append(np.linalg.norm(r) / bn)
             if hist[-1] < target:
                 break
+            if adaptive_n > 0 and n_cur < basis.N and hist[-2] < gamma * hist[-1]:
+                n_cur += 1            # ||r_k|| / ||r_{k+1}|| < gamma
             y = Minv(r)
             rho_new = r @ y
             if beta == "fr":
@@ -197,8 +233,8 @@ def rbcg(basis: Basis, mu, tol=1e-10, max_iter=5000, smoother="rbgs", nu=1,
         r_true = b - pb.apply(prob, mu, x)
         rel = np.linalg.norm(r_true) / bn
         if rel < tol or it >= max_iter:
-            return SolveResult(x, it, rel, rel < tol, hist, restarts)
+            return SolveResult(x, it, rel, rel < tol, hist, restarts, n_hist)
         r = r_true
         hist[-1] = rel
         restarts += 1
-        target = 0.5 * tol
+        target = restart_factor * tol

@@ -3,9 +3,16 @@
 Contents, for the 512 x 512, 3 x 3-block, two-bump workload with n = 40:
   * `selected`: the training indices chosen by the oracle's greedy (Alg. 1,
     sparse-direct snapshots, snapshot-basis L1 score);
-  * `iters`: the oracle's Alg. 3 iteration counts (PR beta, one red-black
-    Gauss-Seidel sweep, tol 1e-10) for the first 16 test parameters, solved
-    with the basis rebuilt from `selected`.
+  * `iters`, `rel_res`, `restarts`: the oracle's Alg. 3 (PR beta, one
+    red-black Gauss-Seidel sweep, tol 1e-10, the plain stopping rule: no
+    restart aims below tol) for the first 16 test parameters, solved with the
+    basis rebuilt from `selected`;
+  * `iters_nu6`, `restarts_nu6`: the same with six red-black sweeps per
+    preconditioner application (the sweep count the GPU benchmark's
+    autotuner picks on this workload);
+  * `*_half`: the same solves when a restarted cycle aims at half the
+    tolerance (restart_factor 0.5), the CUDA library's FP64 restart policy,
+    for comparing its iteration counts.
 It calls only `oracle/` and `workloads`.  Run: python tests/golden/make_golden.py
 """
 from __future__ import annotations
@@ -23,6 +30,8 @@ N_TEST = 16
 
 
 def _worker_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
 
@@ -30,11 +39,11 @@ def _worker_init():
 def _solve(args):
     import workloads as wl
     from oracle import rb
-    W, ANq, fNr, mu, beta = args
+    W, ANq, fNr, mu, beta, nu, rf = args
     w = wl.rbcg_2d_512()
     basis = rb.Basis(w.problem, W, ANq, fNr)
-    res = rb.rbcg(basis, mu, tol=1e-10, beta=beta)
-    return res.iters, res.rel_res, res.converged
+    res = rb.rbcg(basis, mu, tol=1e-10, beta=beta, nu=nu, restart_factor=rf)
+    return res.iters, res.rel_res, res.converged, res.restarts
 
 
 def main():
@@ -49,15 +58,28 @@ def main():
     mu = w.test_mu(N_TEST)
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(N_TEST, os.cpu_count() or 1), initializer=_worker_init) as pool:
-        res = pool.map(_solve, [(basis.W, basis.ANq, basis.fNr, mu[i], "pr") for i in range(N_TEST)])
+        runs = {}
+        for nu in (1, 6):
+            for rf in (1.0, 0.5):
+                runs[nu, rf] = pool.map(_solve, [(basis.W, basis.ANq, basis.fNr, mu[i], "pr", nu, rf)
+                                                 for i in range(N_TEST)])
+        res, res6 = runs[1, 1.0], runs[6, 1.0]
     out = {
         "workload": w.name,
-        "source": "oracle greedy (Alg. 1) and oracle RBCG (Alg. 3, PR beta, rbgs nu=1, tol 1e-10)",
+        "source": "oracle greedy (Alg. 1) and oracle RBCG (Alg. 3, PR beta, rbgs nu=1 and nu=6, tol 1e-10, plain stopping rule)",
         "selected": [int(s) for s in basis.selected],
         "test_indices": list(range(N_TEST)),
         "iters": [int(r[0]) for r in res],
         "rel_res": [float(r[1]) for r in res],
         "converged": [bool(r[2]) for r in res],
+        "restarts": [int(r[3]) for r in res],
+        "iters_nu6": [int(r[0]) for r in res6],
+        "rel_res_nu6": [float(r[1]) for r in res6],
+        "restarts_nu6": [int(r[3]) for r in res6],
+        "iters_half": [int(r[0]) for r in runs[1, 0.5]],
+        "restarts_half": [int(r[3]) for r in runs[1, 0.5]],
+        "iters_nu6_half": [int(r[0]) for r in runs[6, 0.5]],
+        "restarts_nu6_half": [int(r[3]) for r in runs[6, 0.5]],
         "greedy_seconds": round(t_greedy, 1),
     }
     with open(OUT, "w") as f:
