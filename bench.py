@@ -27,26 +27,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RB-PCG solves/sec to rel. residual 1e-10 (mixed+batched vs FP64 plain), % HBM roofline"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
+TUNE_SAMPLE = 256          # training parameters the autotuner times (never the timed test queries)
+PARITY_SEED = 7
 
-# DRAM bytes per grid point and query measured by ncu for the dominant kernel (256-query case,
-# profiles/rbcg_2d_512_smoother_staged.md); scaled to a full launch by its units.
-NCU_TRAFFIC = {("f32", "f32", "smooth"): {"intermediate": 11.57, "last": 15.86,
-                                          "source": "profiles/rbcg_2d_512_smoother_staged.md"}}
-
-# Algorithmic bytes per grid point per launch unit (one query, one pass), by kernel
-# and inner precision: every operand read or written once (eq. 5-8 and Alg. 3 steps).
+# Algorithmic bytes per grid point per launch unit (one query, one application), by kernel and
+# inner precision: every operand read or written once (eqs. 5-8 and the steps of Alg. 3).  The
+# smoother's unit is one preconditioner application, whatever the sweep count: it reads its
+# source y and r, reads the direction p for the Polak-Ribiere term and writes y.
 BYTES_PER_POINT = {
     "f32": {"cg_a": 12, "cg_b": 20, "smooth": 16, "project": 4, "tc_project": 4, "prolong": 4, "tc_prolong": 4,
             "outer_residual": 12, "outer_update": 24},
     "f64": {"cg_a": 24, "cg_b": 40, "smooth": 32, "project": 8, "prolong": 8, "outer_residual": 16},
 }
-# With BF16 storage of the preconditioner's intermediate vectors: the prolongation writes
-# 2 B; a sweep before the last reads source (2) and r (4) and writes 2; the last reads
-# source (2), r (4), p (4) and writes y (4).
+# Bytes per point of one streaming pass of a red-black sweep before the last (source, r, output):
+# the smoother that runs one pass per sweep moves this much more per extra sweep.
+SWEEP_PASS_BYTES = {"f32": 12, "f64": 24}
+# With BF16 storage of the preconditioner's intermediate vectors: the prolongation writes 2 B;
+# a pass before the last reads source (2) and r (4) and writes 2; the last reads source (2), r (4),
+# p (4) and writes y (4).
 BF16_SMOOTH_LAST, BF16_SMOOTH_SWEEP, BF16_PROLONG = 14, 8, 2
 
+# DRAM bytes per point and query of the dominant kernel from an ncu capture, valid only while the
+# kernel's source files hash to what they were when the counters were taken (otherwise the line
+# reports traffic null).  Filled from a capture of the current kernels.
+NCU_TRAFFIC = {}
 
-def parse():
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -58,10 +65,14 @@ def parse():
     ap.add_argument("--nu", type=int, default=1)
     ap.add_argument("--gemm", default="auto")
     ap.add_argument("--kernels", type=int, default=0, help="stencil kernel family (rb_opts.kernels)")
-    ap.add_argument("--fp64-queries", type=int, default=256, help="queries of the FP64 plain comparator (0: skip)")
+    ap.add_argument("--fp64-queries", type=int, default=0,
+                    help="queries of the FP64 plain comparator (default: the timed batch; -1: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=300,
-                    help="Alg. 3 iterations per core in the CPU sample (about 10 s of oracle work)")
+    ap.add_argument("--cpu-nu", type=int, default=6,
+                    help="reference arm: smoother sweeps of the oracle (the GPU arm's tuned value on the default "
+                         "workload); the GPU arm's own CPU baseline uses its tuned value")
+    ap.add_argument("--cpu-iters", type=int, default=60,
+                    help="reference arm: Alg. 3 iterations per core and step (about 10 s of oracle work)")
     ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --nu, --gemm as given)")
     ap.add_argument("--quick", action="store_true",
@@ -72,7 +83,12 @@ def parse():
     ap.add_argument("--warm-pairs", type=int, default=4096, help="training pairs (truth solves) of the network")
     ap.add_argument("--warm-steps", type=int, default=2000, help="Adam steps of the network")
     ap.add_argument("--warm-test", type=int, default=0, help="test queries of the comparison (default: the step's)")
-    return ap.parse_args()
+    ap.add_argument("--no-leg3d", action="store_true",
+                    help="skip the 3D leg (128^3, 256 queries per step, timed after the 2D results)")
+    ap.add_argument("--leg3d-steps", type=int, default=2)
+    ap.add_argument("--rank-check", action="store_true",
+                    help="CPU only: start the ranks, shard the queries and agree on the max time over gloo")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -80,6 +96,44 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def launch_ranks(n: int, argv) -> int:
+    """Run this script as n ranks (one process per GPU) under torch.distributed.run on 127.0.0.1
+    and return the exit code of the launcher.  Used when --gpus N > 1 is given outside a launcher."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+    return subprocess.run(cmd).returncode
+
+
+def rank_check(args):
+    """--rank-check: the multi-rank path without a GPU (gloo): each rank takes its shard of the
+    timed batch, the step time is the max over ranks, rank 0 prints one JSON line."""
+    import torch.distributed as dist
+
+    import workloads as wl
+    from paper_1804_06363_gb300.shard import max_over_ranks, shard_range
+    rank, world, _ = dist_env()
+    if world > 1:
+        dist.init_process_group("gloo")
+    w = wl.WORKLOADS[args.workload]()
+    B = args.batch or w.batch
+    lo, hi = shard_range(B * world, rank, world)
+    t = max_over_ranks(1.0 + rank, dist, "cpu")
+    shards = [None] * world
+    if world > 1:
+        dist.all_gather_object(shards, (rank, lo, hi))
+    else:
+        shards = [(0, lo, hi)]
+    if rank == 0:
+        print(json.dumps({"rank_check": True, "n_ranks": world, "queries": B * world, "shards": shards,
+                          "t_max": t}))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 class Clocks:
@@ -139,49 +193,83 @@ def load_golden():
     return None
 
 
-def cpu_sample(workload_name, n_cores, iters_per_core, steps=1):
-    """Time the oracle's Alg. 3 on the host cores; returns a cpu_baseline-style dict."""
+def base_options(precision: str, stream) -> dict:
+    """Options of the timed solves before tuning: PR beta, red-black GS."""
+    return dict(precision=precision, beta="pr", nu=1, gemm="auto", kernels=0, stream=stream)
+
+
+def tune(ctx, w, x, opts, n_sample: int = TUNE_SAMPLE):
+    """The autotuner on the workload's first n_sample training parameters (never the timed test
+    queries); updates opts with its choice and returns the summary."""
+    tB = min(x.shape[0], n_sample)
+    tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
+    opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
+                store=tuned["store"])
+    tuned["sample"] = f"{tB} training parameters"
+    return tuned
+
+
+def parity_sample(B: int, k: int):
+    """Seeded sample of k query indices of a batch of B (sorted)."""
+    import numpy as np
+    return sorted(int(i) for i in np.random.default_rng(PARITY_SEED).choice(B, min(k, B), replace=False))
+
+
+def source_hash(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1804_06363_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def oracle_runner(workload_name, cores):
+    """The oracle's basis for the workload (from the stored greedy selection) behind a spawn pool."""
     import workloads as wl
     from oracle import baseline
     g = load_golden()
     if g is None or g.get("workload") != wl.WORKLOADS[workload_name]().name:
         return None, "no stored oracle greedy selection for this workload"
-    runner = baseline.OracleRunner(workload_name, g["selected"], n_cores)
-    w = wl.WORKLOADS[workload_name]()
-    mu = w.test_mu(n_cores * max(1, steps))
-    mean_iters = float(sum(g["iters"])) / len(g["iters"])
-    out = []
-    for s in range(steps):
-        its, wall = runner.sample(mu[s * n_cores:(s + 1) * n_cores], iters_per_core)
-        out.append((its, wall))
-    runner.close()
-    return {"mean_iters_per_solve": mean_iters, "samples": out, "setup_s": runner.setup_s}, None
+    return baseline.OracleRunner(workload_name, g["selected"], cores), None
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle (Alg. 3) timed on the host cores."""
+    """--impl reference: the FP64 oracle (Alg. 3) timed on the host cores, each step a bounded sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import workloads as wl
     w = wl.WORKLOADS[args.workload]()
     cores = min(16, os.cpu_count() or 1)
-    res, why = cpu_sample(args.workload, cores, args.cpu_iters, steps=args.warmup + args.steps)
-    if res is None:
+    g = load_golden()
+    key = "iters" if args.cpu_nu == 1 else f"iters_nu{args.cpu_nu}"
+    if g is None or g.get("workload") != w.name or key not in g:
+        print(json.dumps({"impl": "reference", "unavailable": "no stored oracle iteration counts for this "
+                                                              "workload and sweep count"}))
+        return
+    runner, why = oracle_runner(args.workload, cores)
+    if runner is None:
         print(json.dumps({"impl": "reference", "unavailable": why}))
         return
-    timed = res["samples"][args.warmup:]
+    mean_iters = float(sum(g[key])) / len(g[key])
+    mu = w.test_mu(cores * (args.warmup + args.steps))
+    samples = [runner.sample(mu[s * cores:(s + 1) * cores], args.cpu_iters, args.cpu_nu)
+               for s in range(args.warmup + args.steps)]
+    runner.close()
+    timed = samples[args.warmup:]
     its = sum(t[0] for t in timed)
     wall = sum(t[1] for t in timed)
-    value = its / wall / res["mean_iters_per_solve"]
-    sample = (f"{cores} test parameters per step, one per core, {args.cpu_iters} Alg. 3 iterations each; "
-              f"solves/s = iteration rate / the oracle's mean {res['mean_iters_per_solve']:.1f} iterations per "
-              f"solve (tests/golden/rbcg_2d_512_oracle.json)")
+    value = its / wall / mean_iters
+    sample = (f"{cores} test parameters per step, one per core, {args.cpu_iters} Alg. 3 iterations each with "
+              f"{args.cpu_nu} red-black sweeps; solves/s = iteration rate / the oracle's mean {mean_iters:.1f} "
+              f"iterations per solve at that sweep count (stored oracle counts of 16 complete solves)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, len(timed)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "solver": "oracle FP64 Alg. 3 (numpy)",
-                                            "cores": cores},
+                                            "smoother": f"red-black GS nu={args.cpu_nu}", "beta": "pr",
+                                            "tol": 1e-10, "cores": cores},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -276,8 +364,103 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
     return out
 
 
+def leg_3d(args, dev, stream, peak, peak_kind):
+    """The 3D workload (128^3, P = 8, n = 60, 256 queries per step) on the same GPU after the 2D
+    results: basis built by the GPU greedy (snapshots by mixed-precision RBCG to 1e-11), the
+    autotuner on 64 training parameters, warm-up, timed steps with their own clock record, then a
+    per-kernel pass for the roofline of its dominant kernel."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+    w = wl.batched_3d_128()
+    prob = w.problem
+    B, N = w.batch, prob.n_dof
+    t0 = time.perf_counter()
+    ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B, precision="mixed", stream=stream.cuda_stream)
+    build_s = time.perf_counter() - t0
+    progress(f"3D leg: basis of {w.name} ready in {build_s:.1f} s")
+    mu = np.ascontiguousarray(w.test_mu(B))
+    x = torch.zeros((B, N), dtype=torch.float64, device=dev)
+    opts = base_options("mixed", stream.cuda_stream)
+    tuned = tune(ctx, w, x, opts, n_sample=64)
+    progress(f"3D leg: autotuned {tuned}")
+    ctx.pcg(mu, x, **opts)
+    torch.cuda.synchronize()
+    clk = Clocks(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.leg3d_steps):
+        status, st = ctx.pcg(mu, x, **opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    secs = e0.elapsed_time(e1) / 1000.0
+    value = B * args.leg3d_steps / secs
+    progress(f"3D leg: {value:.1f} solves/s, mean iterations {float(st['iters'].mean()):.1f}")
+    ctx.profile(True)
+    _, stp = ctx.pcg(mu, x, **opts)
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    kernels, units = kernel_table(prof, "f32", opts, N, int(stp["iters"].sum()), int(stp["outer"].sum()))
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    achieved = kernels[dom].get("gbs")
+    n_launch = max(1, kernels[dom]["launches"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": None, "peak_source": peak_kind,
+                "alg_bytes_per_unit": kernels[dom].get("alg_bytes_per_point"),
+                "alg_bytes_per_launch": round((kernels[dom].get("alg_bytes") or 0) / n_launch)}
+    if "pass_gbs" in kernels[dom]:
+        roofline["per_pass"] = {"bytes_per_point": kernels[dom]["pass_bytes_per_point"],
+                                "achieved": kernels[dom]["pass_gbs"], "frac": round(kernels[dom]["pass_gbs"] / peak, 4)}
+    out = {"workload": w.name, "metric": "RB-PCG solves/sec to rel. residual 1e-10", "value": value,
+           "unit": "solves/s", "steps": args.leg3d_steps, "warmup": 1, "ms_per_step": 1000.0 * secs / args.leg3d_steps,
+           "queries_per_step": B, "grid": "x".join(map(str, prob.dims)), "P": prob.P, "n_basis": w.n_basis,
+           "all_converged": bool(np.all(st["status"] == rb.RB_OK)), "mean_iters": float(st["iters"].mean()),
+           "max_rel_res": float(st["rel_res"].max()), "autotuned": tuned, "offline_build_s": round(build_s, 1),
+           "roofline": roofline, "kernels": kernels, "clocks": clocks,
+           "l2": "inputs larger than L2 (FP64 solutions %.1f GB per step)" % (B * N * 8 / 1e9)}
+    ctx.close()
+    return out
+
+
+def kernel_table(prof, prec, opts, N, iters, outers):
+    """Per-kernel device time and algorithmic bytes from the rb_profile counters."""
+    nu = max(1, opts["nu"])
+    units = {"cg_a": iters, "cg_b": iters, "smooth": iters, "project": iters, "tc_project": iters,
+             "prolong": iters, "tc_prolong": iters, "outer_residual": outers, "outer_update": outers}
+    bf16 = prec == "f32" and opts.get("store", "f32") == "bf16"
+    kernels = {}
+    for k, (n_launch, ms) in prof.items():
+        bpp = BYTES_PER_POINT[prec].get(k)
+        if bf16 and k in ("prolong", "tc_prolong"):
+            bpp = BF16_PROLONG
+        entry = {"launches": n_launch, "ms": round(ms, 3)}
+        if bpp is not None and ms > 0:
+            alg = bpp * N * units[k]
+            entry["alg_bytes"] = alg
+            entry["alg_bytes_per_point"] = bpp
+            entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
+            if k == "smooth":
+                # the streaming passes of the one-pass-per-sweep smoother, nu per application
+                if bf16:
+                    pas = BF16_SMOOTH_LAST + BF16_SMOOTH_SWEEP * (nu - 1)
+                else:
+                    pas = bpp + SWEEP_PASS_BYTES[prec] * (nu - 1)
+                entry["pass_bytes_per_point"] = pas
+                entry["pass_gbs"] = round(pas * N * units[k] / (ms / 1000.0) / 1e9, 1)
+        kernels[k] = entry
+    return kernels, units
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))
+    if args.rank_check:
+        rank_check(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -299,12 +482,31 @@ def main():
     B = args.batch or w.batch
     N = prob.n_dof
 
+    # ---- CPU baseline (rank 0, one GPU only): a spawn pool of oracle processes rebuilds the
+    #      oracle's basis in the background while the GPU works
+    cores = min(16, os.cpu_count() or 1)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick
+    cpu_setup = {}
+
+    def start_oracle():
+        try:
+            cpu_setup["runner"], cpu_setup["why"] = oracle_runner(args.workload, cores)
+        except Exception as e:  # the baseline must not sink the GPU number
+            cpu_setup["runner"], cpu_setup["why"] = None, f"oracle set-up failed: {type(e).__name__}: {e}"
+
+    oracle_thread = None
+    if want_cpu:
+        import threading
+        oracle_thread = threading.Thread(target=start_oracle, daemon=True)
+        oracle_thread.start()
+
     # ---- offline (not timed): greedy basis on the GPU
     t0 = time.perf_counter()
     if args.basis and os.path.exists(args.basis):
         ctx = rb.Context.load(args.basis, max_batch=B)
     else:
-        ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B)
+        ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B, precision="mixed",
+                               stream=torch.cuda.current_stream(dev).cuda_stream)
         if args.basis:
             ctx.save(args.basis)
     offline_s = time.perf_counter() - t0
@@ -318,17 +520,13 @@ def main():
     mu = np.ascontiguousarray(mu_all[lo:hi])
     x = torch.zeros((B, N), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = dict(precision=args.precision, beta="pr", nu=args.nu, gemm=args.gemm, kernels=args.kernels,
-                stream=stream.cuda_stream)
+    opts = base_options(args.precision, stream.cuda_stream)
+    opts.update(nu=args.nu, gemm=args.gemm, kernels=args.kernels)
 
     # ---- autotuner (setup, not timed): on training parameters, never on the timed test queries
     tuned = None
     if not args.no_tune:
-        tB = min(B, 256)
-        tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
-        opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
-                    store=tuned["store"])
-        tuned["sample"] = f"{tB} training parameters"
+        tuned = tune(ctx, w, x, opts)
         progress(f"autotuned: {tuned}")
 
     def step(xbuf, **kw):
@@ -374,7 +572,7 @@ def main():
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
                               "quick": True, "all_converged": ok, "mean_iters": float(last["iters"].mean()),
                               "config": {"workload": w.name, "queries_per_step_per_gpu": B, "autotuned": tuned},
-                              "warm_start": warm}))
+                              "clocks": clocks, "warm_start": warm}))
         ctx.close()
         if world > 1:
             dist.destroy_process_group()
@@ -390,72 +588,52 @@ def main():
     prec = "f32" if args.precision == "mixed" else "f64"
     iters = int(st_prof["iters"].sum())
     outers = int(st_prof["outer"].sum())
-    units = {"cg_a": iters, "cg_b": iters, "smooth": iters * max(1, opts["nu"]), "project": iters,
-             "tc_project": iters, "prolong": iters, "tc_prolong": iters, "outer_residual": outers,
-             "outer_update": outers}
-    kernels = {}
-    es = 4 if prec == "f32" else 8
-    bf16 = prec == "f32" and opts.get("store", "f32") == "bf16"
-    for k, (n_launch, ms) in prof.items():
-        bpp = BYTES_PER_POINT[prec].get(k)
-        if bf16 and k in ("prolong", "tc_prolong"):
-            bpp = BF16_PROLONG
-        entry = {"launches": n_launch, "ms": round(ms, 3)}
-        if bpp is not None and ms > 0:
-            alg = bpp * N * units[k]
-            if k == "smooth":   # nu sweeps: the last one also reads the direction p (PR term)
-                if bf16:
-                    bpp = BF16_SMOOTH_LAST
-                    alg = (BF16_SMOOTH_LAST + BF16_SMOOTH_SWEEP * (max(1, opts["nu"]) - 1)) * N * iters
-                else:
-                    alg = (bpp + 3 * es * (max(1, opts["nu"]) - 1)) * N * iters
-            entry["alg_bytes"] = alg
-            entry["alg_bytes_per_point"] = round(alg / (N * max(1, units[k] if k != "smooth" else iters)), 2)
-            entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
-        kernels[k] = entry
+    kernels, units = kernel_table(prof, prec, opts, N, iters, outers)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     peak, peak_kind = measured_peaks()
     achieved = kernels[dom].get("gbs")
-    traffic = None
-    nt = NCU_TRAFFIC.get((prec, opts.get("store", "f32"), dom))
-    if nt is not None and dom == "smooth" and kernels[dom]["launches"]:
-        # one "smooth" launch = nu sweeps; bytes scaled to the average launch of this run
-        per_launch_units = iters / kernels[dom]["launches"]
-        traffic = round((nt["intermediate"] * (opts["nu"] - 1) + nt["last"]) * N * per_launch_units)
-    alg_per_launch = (kernels[dom].get("alg_bytes") or 0) / max(1, kernels[dom]["launches"])
+    n_launch = max(1, kernels[dom]["launches"])
+    traffic, traffic_src = None, None
+    nt = NCU_TRAFFIC.get((prec, opts.get("store", "f32"), dom, opts["nu"]))
+    if nt is not None and source_hash(nt["sources"]) == nt["sha"]:
+        traffic = round(nt["bytes_per_point"] * N * units[dom] / n_launch)
+        traffic_src = nt["capture"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
-                "traffic_source": nt["source"] if nt else None,
-                "peak_source": peak_kind,
+                "traffic_capture": traffic_src, "peak_source": peak_kind,
                 "alg_bytes_per_unit": kernels[dom].get("alg_bytes_per_point"),
-                "alg_bytes_per_launch": round(alg_per_launch),
-                "unit_def": "one query x one grid point x one launch (smooth: the nu sweeps of one preconditioner application)"}
+                "alg_bytes_per_launch": round((kernels[dom].get("alg_bytes") or 0) / n_launch),
+                "unit_def": "one query x one grid point x one application of the kernel (each operand touched once)"}
+    if "pass_gbs" in kernels[dom]:
+        roofline["per_pass"] = {"bytes_per_point": kernels[dom]["pass_bytes_per_point"],
+                                "achieved": kernels[dom]["pass_gbs"],
+                                "frac": round(kernels[dom]["pass_gbs"] / peak, 4),
+                                "what": f"one streaming pass per red-black sweep ({opts['nu']} per application)"}
 
     # ---- end to end through the C interface with host buffers (pinned)
     xh = torch.zeros((B, N), dtype=torch.float64, pin_memory=True).numpy()
     ctx.pcg(mu, xh, **{**opts, "stream": stream.cuda_stream})
     torch.cuda.synchronize()
+    e2e_steps = min(args.steps, 10)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         ctx.pcg(mu, xh, **opts)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * B * args.steps / e2e_s if world == 1 else None, "unit": "solves/s",
-           "h2d_bytes_per_step": int(mu.nbytes), "d2h_bytes_per_step": int(B * N * 8 + B * 24)}
-    if world > 1:
-        e2e["value"] = world * B * args.steps / max_over_ranks(e2e_s, dist, dev)
+    e2e = {"value": world * B * e2e_steps / max_over_ranks(e2e_s, dist, dev), "unit": "solves/s",
+           "steps": e2e_steps, "h2d_bytes_per_step": int(mu.nbytes), "d2h_bytes_per_step": int(B * N * 8 + B * 24)}
 
-    # ---- FP64 plain comparator (same GPU, same workload, fewer queries)
+    # ---- FP64 plain comparator: the paper's method in FP64 on the same GPU, the same queries,
+    #      its sweep count tuned on the same training sample as the mixed arm
     fp64 = None
-    if args.fp64_queries > 0 and args.precision == "mixed":
-        q64 = min(B, args.fp64_queries)
-        x64 = torch.zeros((q64, N), dtype=torch.float64, device=dev)
-        opts64 = {**opts, "precision": "fp64"}
+    if args.fp64_queries >= 0 and args.precision == "mixed":
+        q64 = B if args.fp64_queries == 0 else min(B, args.fp64_queries)
+        x64 = x[:q64]
+        opts64 = base_options("fp64", stream.cuda_stream)
         tuned64 = None
         if not args.no_tune:
-            tuned64 = ctx.autotune(w.train_mu()[:64], x64[:64], **opts64)
-            opts64.update(nu=tuned64["nu"])
-        ctx.pcg(mu[:q64], x64, **opts64)
+            tuned64 = tune(ctx, w, x64, opts64)
+        ctx.pcg(mu[:min(q64, 64)], x64[:min(q64, 64)], **opts64)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -463,28 +641,56 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         s64 = a.elapsed_time(b) / 1000.0
-        fp64 = {"value": q64 / s64, "unit": "solves/s", "queries": q64, "nu": opts64["nu"],
-                "tuned": tuned64,
+        fp64 = {"value": q64 / s64, "unit": "solves/s", "queries": q64, "nu": opts64["nu"], "tuned": tuned64,
                 "mean_iters": float(st64["iters"].mean()), "all_converged": bool(np.all(st64["status"] == 0)),
-                "max_rel_res": float(st64["rel_res"].max())}
+                "max_rel_res": float(st64["rel_res"].max()), "mixed_over_fp64": round(value / (q64 / s64), 2)}
+        progress(f"FP64 comparator: {fp64['value']:.1f} solves/s on {q64} queries (nu {opts64['nu']})")
+        # the timed solutions again (x was overwritten by the comparator), for the parity check
+        step(x)
+        torch.cuda.synchronize()
 
-    # ---- CPU baseline (rank 0, one GPU only)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = min(16, os.cpu_count() or 1)
+    # ---- CPU baseline and parity (rank 0, one GPU): complete oracle solves of a seeded sample of
+    #      the timed queries at the GPU arm's sweep count; the oracle's sparse-direct truth of the
+    #      same queries gives the error of the GPU's solutions per result
+    cpu, parity = None, None
+    runner, cpu_why = None, None
+    if oracle_thread is not None:
+        oracle_thread.join()
+        runner, cpu_why = cpu_setup.get("runner"), cpu_setup.get("why")
+    if want_cpu and runner is not None:
         try:
-            res, why = cpu_sample(args.workload, cores, args.cpu_iters, steps=1)
+            idx = parity_sample(B, cores)
+            wall, out = runner.solve([mu[i] for i in idx], opts["nu"])
+            its = [o[0] for o in out]
+            cpu = {"value": len(idx) / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": (f"{len(idx)} complete solves of seeded test queries of the timed batch, one per core, "
+                              f"oracle FP64 Alg. 3 with the GPU arm's {opts['nu']} red-black sweeps, PR beta, "
+                              f"tol 1e-10 ({wall:.1f} s wall, {np.mean(its):.1f} iterations per solve)"),
+                   "mean_iters": float(np.mean(its)), "all_converged": all(o[3] < 1e-10 for o in out)}
+            xs = x.cpu().numpy()
+            errs = runner.errors([mu[i] for i in idx], [[xs[i], out[k][4]] for k, i in enumerate(idx)])
+            e_gpu = [e[0][0] for e in errs]
+            r_gpu = [e[0][1] for e in errs]
+            e_orc = [e[1][0] for e in errs]
+            parity = {"queries": idx, "truth": "oracle sparse-direct solve of eq. 1 (FP64)",
+                      "gpu_rel_err": e_gpu, "max_rel_err": max(e_gpu), "median_rel_err": float(np.median(e_gpu)),
+                      "max_oracle_rel_res_of_gpu": max(r_gpu), "oracle_rbcg_max_rel_err": max(e_orc),
+                      "bar": 1e-9, "pass": max(e_gpu) <= 1e-9 and max(r_gpu) < 1e-10}
+            progress(f"parity: max rel. error {parity['max_rel_err']:.3g} over {len(idx)} queries; "
+                     f"CPU baseline {cpu['value']:.3f} solves/s")
         except Exception as e:  # the baseline must not sink the GPU number
-            res, why = None, f"oracle sample failed: {e}"
-        if res is not None:
-            its, wall = res["samples"][0]
-            cpu = {"value": its / wall / res["mean_iters_per_solve"], "unit": "solves/s", "cores": cores,
-                   "kind": "oracle",
-                   "sample": (f"{cores} test parameters, one per core, {args.cpu_iters} iterations of the oracle's "
-                              f"FP64 Alg. 3 each ({its} in {wall:.1f} s); solves/s = iteration rate / the oracle's "
-                              f"mean {res['mean_iters_per_solve']:.1f} iterations per solve")}
-        else:
-            cpu = {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": why}
+            cpu = {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": f"oracle run failed: {type(e).__name__}: {e}"}
+        runner.close()
+    elif want_cpu:
+        cpu = {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": cpu_why}
+
+    leg3d = None
+    if rank == 0 and world == 1 and not args.no_leg3d and args.workload == "rbcg_2d_512":
+        try:
+            leg3d = leg_3d(args, dev, stream, peak, peak_kind)
+        except Exception as e:  # the 3D leg must not sink the headline number
+            leg3d = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {
@@ -503,10 +709,12 @@ def main():
             "all_converged": ok, "mean_iters": float(last["iters"].mean()), "max_iters": int(last["iters"].max()),
             "mean_outer": float(last["outer"].mean()), "max_rel_res": float(last["rel_res"].max()),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
-            "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu, "parity": parity, "clocks": clocks,
         }
         if warm is not None:
             line["warm_start"] = warm
+        if leg3d is not None:
+            line["leg_3d"] = leg3d
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -90,7 +90,9 @@ typedef struct {
                               memory by bulk asynchronous copies;
                            1: as 0, but all red-black sweeps fused in one pass (FP32 mixed path,
                               nu <= 6);
-                           2: CG body and one smoother pass per sweep with rows held in registers.
+                           2: CG body and one smoother pass per sweep with rows held in registers;
+                           3: as 0, but up to three red-black sweeps per pass over memory (FP32
+                              mixed path with FP32 storage; other cases as 0).
                            On 3D grids (RBCG): 0 marches the CG body and the red-black smoother in
                            z with planes prefetched into shared memory by asynchronous copies;
                            1 the smoother marching in z with direct loads and the generic CG
@@ -101,6 +103,12 @@ typedef struct {
                            preconditioned residual y is FP32.  It applies to the mixed solver with
                            the red-black smoother and kernels = 0 on 2D grids whose rows hold a
                            multiple of 128 points; elsewhere the storage is FP32. */
+    int adaptive_n;     /* RBCG only (rb_pcg; rb_solve ignores it).  0: every preconditioner
+                           application uses the whole basis.  k >= 1: the adaptive choice of N at the
+                           end of Section 4.1: start with the first k basis vectors (W_k, nested in W_n)
+                           and use one more after every iteration whose recurrence residual fell by
+                           less than gamma, ||r_k|| / ||r_{k+1}|| < gamma, up to n. */
+    double gamma;       /* ratio of that test (the paper suggests 10) */
     void* stream;       /* cudaStream_t or NULL */
 } rb_opts;
 
@@ -110,6 +118,7 @@ typedef struct {
     int restarts;       /* residual replacements after a failed true-residual check */
     int status;         /* rb_status of this query */
     double rel_res;     /* final true ||f - A x|| / ||f|| in FP64 */
+    int n_used;         /* basis vectors of the last preconditioner application (n unless adaptive) */
 } rb_stats;
 
 typedef struct {
@@ -121,7 +130,7 @@ typedef struct {
 
 /* Fill defaults: tol 1e-10, red-black Gauss-Seidel with nu = 1, FP64, PR beta,
  * zero start, inner_tol 1e-5, max_outer 12, automatic GEMM engine, graphs on,
- * staged kernels (kernels = 0), FP32 storage. */
+ * staged kernels (kernels = 0), FP32 storage, fixed N (adaptive_n 0, gamma 10). */
 void rb_default_opts(rb_opts* opts);
 void rb_default_build_opts(rb_build_opts* opts);
 
@@ -139,8 +148,9 @@ rb_status rb_offline_load_arrays(rb_ctx** out, const rb_problem* prob, int n,
                                  int max_batch);
 
 /* Offline greedy (Alg. 1 steps, snapshots solved on the device by RBCG with
- * W_{N-1} as in Alg. 4; Gram-Schmidt twice; eq. 12c grown one row and column
- * per step).  mu_train host [n_train][n_mu]; the first training vector is mu_1.
+ * W_{N-1} as in Alg. 4, in solve_opts->precision: FP64, or FP32 inner RBCG with
+ * FP64 residual refinement, both to the FP64 relative residual truth_tol;
+ * Gram-Schmidt twice; eq. 12c grown one row and column per step).  mu_train host [n_train][n_mu]; the first training vector is mu_1.
  * Produces a context with n = n_max basis vectors (fewer if the training set
  * runs out of independent snapshots). */
 rb_status rb_offline_build(rb_ctx** out, const rb_problem* prob, int n_max, int n_train,
@@ -180,6 +190,22 @@ rb_status rb_solve(rb_ctx* ctx, int B, const double* mu, double* x,
  */
 rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x,
                  const rb_opts* opts, rb_stats* stats);
+
+/*
+ * Ragged batch: several problems, each with its own context (grid, basis and
+ * workspace), solved by RBCG (Alg. 3, as rb_pcg) in one launch sequence.  Each
+ * round enqueues the next steps of every unfinished context on that context's
+ * own stream, so the kernels of the different grids run side by side on the
+ * GPU, then polls them all.  ctxs [nctx] distinct contexts (nctx <= 16);
+ * B [nctx] queries of each (0 .. max_batch of that context, one wave each);
+ * mu [nctx] host [B[c]][n_mu]; x [nctx] device [B[c]][N_dof] of context c;
+ * stats [nctx] host [B[c]] each, or stats NULL; opts as rb_pcg (opts->stream,
+ * when set, is waited for first; the contexts then use their own streams).
+ * Returns the worst status over all queries; errors of a context go to its
+ * rb_last_error, argument errors before any context to rb_last_error(NULL).
+ */
+rb_status rb_pcg_ragged(rb_ctx* const* ctxs, int nctx, const int* B, const double* const* mu, double* const* x,
+                        const rb_opts* opts, rb_stats* const* stats);
 
 /* The two batched products of the RB preconditioner in FP32 storage, with the
  * engine of the mixed path: WtR[b] = W^T R[b] (eq. 5, as in Alg. 2 step 4) and
@@ -326,21 +352,35 @@ void rb_mlp_free(rb_mlp* net);
  * cudaMalloc, such as code running under a framework whose caching allocator
  * holds the device memory, or latency-bound code that cannot accept the
  * device-wide synchronisation an allocation may cause.  It needs no rb_ctx.
- *   prob     the problem, as for rb_offline_load_arrays;
- *   mu       host [B][n_mu];   x  device [B][N_dof] (host memory is rejected);
+ *   prob     the problem, checked as for rb_offline_load_arrays (RB_EINVAL);
+ *   mu       host [B][n_mu];   x  device [B][N_dof] of the current device
+ *            (host memory and another device's memory are rejected, RB_EINVAL);
  *   rel_res  host [B], written; stream as in rb_opts (may be NULL).
  * Scratch: one static 1 MiB device array per GPU that loads the library, held
  * until the process exits.  It must hold B*n_mu + 2*B*ceil(N_dof/1024) + B
  * doubles (each part rounded up to 256 bytes); a larger batch is rejected with
  * RB_EINVAL and a message in rb_last_error(NULL).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
+ * current and keeps it for that device's CUDA context; after a device reset the
+ * next call looks it up again.  Make the first call on a device (and the first
+ * after a reset) before any stream capture.  Every call shares
  * the array and overwrites what it reads, so calls that overlap on the GPU
  * (other threads or streams) race: serialise them.  Synchronous: returns after
  * rel_res is on the host.
  */
 rb_status rb_residual_noalloc(const rb_problem* prob, int B, const double* mu, const double* x,
                               double* rel_res, void* stream);
+
+/* Failure-path test hook.  Every kernel that waits on an asynchronous copy
+ * bounds the wait (2 s by default): on expiry it raises a device error flag,
+ * keeps its barriers matched, lets its copies land (bounded) and returns; the
+ * call then returns RB_ETIMEOUT and the context stays usable.  This sets that
+ * limit to limit_s seconds (0 < limit_s <= 2) and, when skip_stage >= 0, makes
+ * the first CTA of the staged CG part-B kernel (2D grids whose rows hold a
+ * multiple of 128 points) leave its stage number skip_stage unissued, so that
+ * the wait on it runs out without any copy in flight.  rb_debug_wait(ctx, 2.0,
+ * -1) restores the defaults.  The paper has no counterpart. */
+rb_status rb_debug_wait(rb_ctx* ctx, double limit_s, long long skip_stage);
 
 /* Text of the last error on ctx (or of the last failed context creation when
  * ctx is NULL).  Valid until the next call on that context. */

@@ -1,7 +1,9 @@
 """CPU-baseline timing of the oracle (used only by bench.py's CPU legs).
 
 The oracle is timed as it stands: `rb.rbcg` (Alg. 3) on the host cores, one
-process per core (spawn), each single-threaded.  The basis is the oracle's
+process per core (spawn), each single-threaded.  Complete solves give the
+CPU baseline and, with the oracle's sparse-direct truth of the same queries,
+the error of the GPU's solutions (parity stated per result).  The basis is the oracle's
 own: the greedy selection stored by tests/golden/make_golden.py (oracle-only)
 is turned back into W by solving those snapshots with the oracle's sparse
 direct solver (in parallel, they are independent once selected), modified
@@ -35,16 +37,46 @@ def _snapshot(args):
     return direct.sparse_direct(w.problem, mu)
 
 
-def _iterate(args):
-    name, paths, mu, max_iter = args
+def _basis(name, paths):
     import workloads as wl
     from oracle import rb
     w = wl.WORKLOADS[name]()
     W = np.load(paths["W"], mmap_mode="r")
-    basis = rb.Basis(w.problem, np.asarray(W), np.load(paths["ANq"]), np.load(paths["fNr"]))
+    return rb.Basis(w.problem, np.asarray(W), np.load(paths["ANq"]), np.load(paths["fNr"]))
+
+
+def _iterate(args):
+    name, paths, mu, max_iter, nu = args
+    from oracle import rb
+    basis = _basis(name, paths)
     t0 = time.perf_counter()
-    res = rb.rbcg(basis, mu, tol=1e-10, beta="pr", max_iter=max_iter)
+    res = rb.rbcg(basis, mu, tol=1e-10, beta="pr", nu=nu, max_iter=max_iter)
     return res.iters, time.perf_counter() - t0
+
+
+def _solve(args):
+    """One complete Alg. 3 solve (timed); returns (iterations, seconds, restarts, rel_res, x)."""
+    name, paths, mu, nu = args
+    from oracle import rb
+    basis = _basis(name, paths)
+    t0 = time.perf_counter()
+    res = rb.rbcg(basis, mu, tol=1e-10, beta="pr", nu=nu)
+    return res.iters, time.perf_counter() - t0, res.restarts, res.rel_res, res.x
+
+
+def _errors(args):
+    """Relative L2 errors against the sparse-direct truth of eq. 1 and the oracle's relative
+    residual of each given vector: [(err, rel_res) for each vector]."""
+    name, mu, vectors = args
+    import workloads as wl
+    from oracle import direct
+    from oracle import problem as pb
+    prob = wl.WORKLOADS[name]().problem
+    truth = direct.sparse_direct(prob, mu)
+    f = pb.load(prob, mu)
+    tn, fn = np.linalg.norm(truth), np.linalg.norm(f)
+    return [(float(np.linalg.norm(v - truth) / tn), float(np.linalg.norm(f - pb.apply(prob, mu, v)) / fn))
+            for v in vectors]
 
 
 def pool(processes: int):
@@ -84,14 +116,26 @@ class OracleRunner:
             self.paths[k] = os.path.join(self.tmp.name, k + ".npy")
             np.save(self.paths[k], a)
 
-    def sample(self, mus, max_iter: int):
+    def sample(self, mus, max_iter: int, nu: int = 1):
         """Run Alg. 3 on each mu (one per process) for at most max_iter iterations.
 
         Returns (total iterations, wall seconds)."""
         t0 = time.perf_counter()
-        out = self.pool.map(_iterate, [(self.name, self.paths, mu, max_iter) for mu in mus])
+        out = self.pool.map(_iterate, [(self.name, self.paths, mu, max_iter, nu) for mu in mus])
         wall = time.perf_counter() - t0
         return sum(o[0] for o in out), wall
+
+    def solve(self, mus, nu: int):
+        """Complete Alg. 3 solves of every mu (one per process).
+
+        Returns (wall seconds, [(iterations, seconds, restarts, rel_res, x)])."""
+        t0 = time.perf_counter()
+        out = self.pool.map(_solve, [(self.name, self.paths, mu, nu) for mu in mus])
+        return time.perf_counter() - t0, out
+
+    def errors(self, mus, vectors):
+        """Per query, [(relative error vs the truth, oracle relative residual)] of each of its vectors."""
+        return self.pool.map(_errors, [(self.name, mu, vs) for mu, vs in zip(mus, vectors)])
 
     def close(self):
         self.pool.close()

@@ -27,6 +27,49 @@ struct DevBuf {
 namespace rbk {
 // error text of calls that have no context (read back by rb_last_error(NULL))
 void set_global_error(const std::string& m) { g_create_error = m; }
+
+PtrKind pointer_kind(const void* p) {
+    if (!p) return PTR_HOST;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_HOST;
+    }
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+    if (a.type != cudaMemoryTypeDevice) return PTR_HOST;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_OTHER_DEVICE;
+    }
+    return a.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
+}
+
+rb_status validate_problem(const rb_problem* prob, std::string& why) {
+    if (!prob) { why = "problem is NULL"; return RB_EINVAL; }
+    if (prob->dim != 2 && prob->dim != 3) { why = "dim must be 2 or 3"; return RB_EINVAL; }
+    long long P = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (prob->m[d] < 1 || prob->nb[d] < 1 || prob->nb[d] > prob->m[d]) {
+            why = "grid sizes must be >= 1 and blocks must lie in 1..m per direction";
+            return RB_EINVAL;
+        }
+        P *= prob->nb[d];
+    }
+    if (prob->dim == 2 && (prob->m[2] != 1 || prob->nb[2] != 1)) { why = "dim 2 needs m[2] = nb[2] = 1"; return RB_EINVAL; }
+    if (P > MAX_P) { why = "too many blocks (max 64)"; return RB_EINVAL; }
+    if ((long long)prob->m[0] * prob->m[1] * prob->m[2] >= (1LL << 31)) { why = "grid too large (N_dof >= 2^31)"; return RB_EINVAL; }
+    if (prob->n_loads < 1 || prob->n_loads > MAX_LOADS || !prob->loads) { why = "need 1..8 load terms"; return RB_EINVAL; }
+    if (prob->n_mu < P || prob->n_mu > MAX_MU) { why = "n_mu must be in P..128"; return RB_EINVAL; }
+    for (int r = 0; r < prob->n_loads; ++r) {
+        const rb_load& l = prob->loads[r];
+        if (l.kind != RB_LOAD_CONST && l.kind != RB_LOAD_GAUSS) { why = "unknown load kind"; return RB_EINVAL; }
+        if (l.param >= prob->n_mu || l.param < -1) { why = "load parameter index out of range"; return RB_EINVAL; }
+        if (l.kind == RB_LOAD_GAUSS && !(l.sigma > 0.0)) { why = "Gaussian load needs sigma > 0"; return RB_EINVAL; }
+    }
+    return RB_OK;
+}
+
 }  // namespace rbk
 
 struct rb_ctx {
@@ -74,6 +117,12 @@ struct rb_ctx {
     int* d_flag = nullptr;            // breakdown flag of rb_warm_start
     int nsplit_max = 1;
     bool force_generic = false;       // testing: use the generic stencil kernels everywhere
+    unsigned long long wait_ns = 2000000000ull;   // limit of the kernels' bounded waits (rb_debug_wait)
+    long long dbg_skip = -1;                      // test hook of rb_debug_wait
+    // the captured graph of the last solve (reused while its launch parameters stay the same)
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<unsigned char> graph_key;
+    cudaStream_t graph_stream = nullptr;
     // per-kernel timing (rb_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -84,6 +133,7 @@ struct rb_ctx {
     // host
     QState* h_st = nullptr;
     int* h_ndone = nullptr;
+    int* h_err = nullptr;             // device error flag polled with the done counter
     int* h_done = nullptr;
     cudaStream_t own_stream = nullptr;
     cudaStream_t copy_stream = nullptr;   // solutions of finished queries to host buffers
@@ -100,6 +150,15 @@ namespace {
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
             ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+            return RB_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+#define CK_GLOBAL(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            g_create_error = std::string(#call) + ": " + cudaGetErrorString(e_);         \
             return RB_ECUDA;                                                             \
         }                                                                                \
     } while (0)
@@ -125,42 +184,18 @@ rb_status dalloc(rb_ctx* ctx, T** p, size_t count) {
         if (s_ != RB_OK) return s_;   \
     } while (0)
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+// true for device (or managed) memory of the current device, false for host
+// memory; a buffer on another device sets ctx->err and *bad
+bool is_device_ptr(rb_ctx* ctx, const void* p, bool* bad) {
+    const PtrKind k = pointer_kind(p);
+    if (k == PTR_OTHER_DEVICE) {
+        ctx->err = "a buffer lives on another device than the current one";
+        *bad = true;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return k == PTR_DEVICE;
 }
 
 int pad_to(int v, int m) { return ((v + m - 1) / m) * m; }
-
-rb_status validate_problem(const rb_problem* prob, std::string& why) {
-    if (!prob) { why = "problem is NULL"; return RB_EINVAL; }
-    if (prob->dim != 2 && prob->dim != 3) { why = "dim must be 2 or 3"; return RB_EINVAL; }
-    long long P = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (prob->m[d] < 1 || prob->nb[d] < 1 || prob->nb[d] > prob->m[d]) {
-            why = "grid sizes must be >= 1 and blocks must lie in 1..m per direction";
-            return RB_EINVAL;
-        }
-        P *= prob->nb[d];
-    }
-    if (prob->dim == 2 && (prob->m[2] != 1 || prob->nb[2] != 1)) { why = "dim 2 needs m[2] = nb[2] = 1"; return RB_EINVAL; }
-    if (P > MAX_P) { why = "too many blocks (max 64)"; return RB_EINVAL; }
-    if ((long long)prob->m[0] * prob->m[1] * prob->m[2] >= (1LL << 31)) { why = "grid too large (N_dof >= 2^31)"; return RB_EINVAL; }
-    if (prob->n_loads < 1 || prob->n_loads > MAX_LOADS || !prob->loads) { why = "need 1..8 load terms"; return RB_EINVAL; }
-    if (prob->n_mu < P || prob->n_mu > MAX_MU) { why = "n_mu must be in P..128"; return RB_EINVAL; }
-    for (int r = 0; r < prob->n_loads; ++r) {
-        const rb_load& l = prob->loads[r];
-        if (l.kind != RB_LOAD_CONST && l.kind != RB_LOAD_GAUSS) { why = "unknown load kind"; return RB_EINVAL; }
-        if (l.param >= prob->n_mu || l.param < -1) { why = "load parameter index out of range"; return RB_EINVAL; }
-        if (l.kind == RB_LOAD_GAUSS && !(l.sigma > 0.0)) { why = "Gaussian load needs sigma > 0"; return RB_EINVAL; }
-    }
-    return RB_OK;
-}
 
 // Allocate everything of a context for basis capacity n_cap and batch Bmax.
 rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch) {
@@ -294,6 +329,7 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
 
     if (cudaMallocHost((void**)&ctx->h_st, (size_t)B * sizeof(QState)) != cudaSuccess ||
         cudaMallocHost((void**)&ctx->h_ndone, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&ctx->h_done, (size_t)B * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -307,11 +343,13 @@ void ctx_destroy(rb_ctx* ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     tc_free(ctx->tc);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_ndone) cudaFreeHost(ctx->h_ndone);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->h_done) cudaFreeHost(ctx->h_done);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -436,7 +474,16 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bo
                !ctx->force_generic && use_rowmarch(ctx->geo) && use_tma_smoother(ctx->geo))
                   ? 1
                   : 0;
+    P.adaptive = (!m.rbi && o.adaptive_n > 0 && ctx->n > 0) ? 1 : 0;
+    P.gamma = o.gamma;
+    P.wait_ns = ctx->wait_ns;
+    P.dbg_skip = ctx->dbg_skip;
     return P;
+}
+
+// basis vectors of a query's first preconditioner application
+int first_n_used(const rb_ctx* ctx, const rb_opts& o, Mode m) {
+    return (!m.rbi && o.adaptive_n > 0) ? std::min(o.adaptive_n, ctx->n) : ctx->n;
 }
 
 enum KernelKind {
@@ -564,6 +611,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic &&
                 use_fused_smoother(ctx->geo, o.nu))
                 launch2d_smooth_fused(P, L, o.nu);
+            else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 3 && !P.ybf16 && use_multi_smoother(ctx->geo))
+                launch2d_smooth_multi(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
@@ -589,20 +638,80 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
-        (o.kernels < 0 || o.kernels > 2) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
-        (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED)) {
+        (o.kernels < 0 || o.kernels > 3) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
+        (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED) || o.adaptive_n < 0 ||
+        !(o.gamma >= 0.0)) {
         ctx->err = "invalid options";
         return RB_EINVAL;
     }
     return RB_OK;
 }
 
-// Solve one wave of B <= Bmax queries; x64 is a device array [B][N].  With x_host
-// (host [B][N]) the solution of every query is copied there as soon as the query
-// finishes, on a side stream, while the others still iterate.
-rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool x_given, const rb_opts& o, Mode m,
-                   rb_stats* stats, double* x_host) {
-    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
+// One wave of B <= Bmax queries of a context in flight: set up by wave_begin, advanced
+// by wave_launch (8 steps of the state machine, replayed as a CUDA graph) and
+// wave_check (after the stream has been synchronised), closed by wave_end.
+struct Wave {
+    rb_ctx* ctx = nullptr;
+    int B = 0;
+    double* x64 = nullptr;      // device [B][N]
+    double* x_host = nullptr;   // host [B][N] or null: finished solutions are copied there as they finish
+    bool x_given = false;
+    rb_opts o{};
+    Mode m{false, false};
+    cudaStream_t s = nullptr;
+    Params P{};
+    Launch L{};
+    bool use_tc = false;
+    cudaGraphExec_t exec = nullptr;
+    long long steps = 0, max_steps = 0;
+    int copied = 0;
+    rb_status rs = RB_OK;
+    bool finished = false;
+};
+
+constexpr int CHECK_EVERY = 8;   // state-machine steps per graph replay (between host polls)
+
+// The captured graph of CHECK_EVERY steps is kept per context and reused while the launch
+// parameters are the same (the usual case of repeated calls with the same buffers).
+rb_status wave_graph(Wave& w) {
+    rb_ctx* ctx = w.ctx;
+    std::vector<unsigned char> key(sizeof(Params) + 6 * sizeof(int));
+    std::memcpy(key.data(), &w.P, sizeof(Params));
+    const int extra[6] = {w.o.nu, w.o.smoother, w.o.kernels, w.m.mixed ? 1 : 0, w.use_tc ? 1 : 0, w.m.rbi ? 1 : 0};
+    std::memcpy(key.data() + sizeof(Params), extra, sizeof(extra));
+    if (ctx->graph_exec && ctx->graph_stream == w.s && key == ctx->graph_key) {
+        w.exec = ctx->graph_exec;
+        return RB_OK;
+    }
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(w.s, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < CHECK_EVERY; ++k) enqueue_step(ctx, w.P, w.L, w.o, w.m, w.use_tc);
+    cudaError_t ce = cudaStreamEndCapture(w.s, &graph);
+    if (ce != cudaSuccess) {
+        ctx->err = std::string("graph capture failed: ") + cudaGetErrorString(ce);
+        return RB_ECUDA;
+    }
+    ce = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        ctx->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ce);
+        return RB_ECUDA;
+    }
+    ctx->graph_key.swap(key);
+    ctx->graph_stream = w.s;
+    w.exec = ctx->graph_exec;
+    return RB_OK;
+}
+
+rb_status wave_begin(Wave& w, const double* mu_host) {
+    rb_ctx* ctx = w.ctx;
+    const int B = w.B;
+    cudaStream_t s = w.s;
     const long long N = ctx->N;
     for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i) {
         if (!std::isfinite(mu_host[i])) {
@@ -616,7 +725,8 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
         std::memset(&st, 0, sizeof(QState));
         st.phase = PH_OUTER;
         st.start = 1;
-        st.xzero = x_given ? 0 : 1;
+        st.xzero = w.x_given ? 0 : 1;
+        st.n_used = first_n_used(ctx, w.o, w.m);
     }
     CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
     std::vector<int> lc(N_LISTS, 0);
@@ -627,79 +737,102 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
     CK(cudaMemcpyAsync(ctx->d_lidx + L_OUT * ctx->Bmax, li.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_ndone, 0, sizeof(int), s));
     CK(cudaMemsetAsync(ctx->d_tick, 0, (size_t)B * sizeof(unsigned), s));
-    if (!x_given) CK(cudaMemsetAsync(x64, 0, (size_t)B * N * sizeof(double), s));
-    if (m.mixed) CK(cudaMemsetAsync(ctx->d_d32, 0, (size_t)B * N * sizeof(float), s));
+    if (!w.x_given) CK(cudaMemsetAsync(w.x64, 0, (size_t)B * N * sizeof(double), s));
+    if (w.m.mixed) CK(cudaMemsetAsync(ctx->d_d32, 0, (size_t)B * N * sizeof(float), s));
+    // the host stages above are freed when the call returns: let them land first
+    CK(cudaStreamSynchronize(s));
 
-    const bool use_tc = m.mixed && o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
-    if (m.mixed && o.gemm == RB_GEMM_TENSOR && !use_tc) {
+    w.use_tc = w.m.mixed && w.o.gemm != RB_GEMM_CUDA_CORES && tc_usable(ctx->tc, ctx->n);
+    if (w.m.mixed && w.o.gemm == RB_GEMM_TENSOR && !w.use_tc) {
         ctx->err = "tensor-core engine unavailable for this problem (needs N_dof % 32 == 0, n >= 1, sm_10x)";
         return RB_EINVAL;
     }
-    Params P = make_params(ctx, B, x64, o, m, use_tc);
-    Launch L{ctx->grid, s};
-    launch_cholesky(P, s, ctx->d_ANq, ctx->P);
+    w.P = make_params(ctx, B, w.x64, w.o, w.m, w.use_tc);
+    w.L = Launch{ctx->grid, s};
+    launch_cholesky(w.P, s, ctx->d_ANq, ctx->P);
     CK(cudaGetLastError());
-    const int check_every = 8;
-    cudaGraphExec_t exec = nullptr;
-    if (o.graph && s != nullptr && !ctx->profiling) {
-        cudaGraph_t graph;
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < check_every; ++k) enqueue_step(ctx, P, L, o, m, use_tc);
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (ce != cudaSuccess) {
-            ctx->err = std::string("graph capture failed: ") + cudaGetErrorString(ce);
-            return RB_ECUDA;
-        }
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) {
-            ctx->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ce);
-            return RB_ECUDA;
-        }
+    w.exec = nullptr;
+    if (w.o.graph && s != nullptr && !ctx->profiling) TRY(wave_graph(w));
+    w.max_steps = (long long)w.o.max_iter + 2LL * w.o.max_outer + 64;
+    return RB_OK;
+}
+
+// enqueue the next CHECK_EVERY steps and the copies of the done counter and error flag
+rb_status wave_launch(Wave& w) {
+    rb_ctx* ctx = w.ctx;
+    if (w.exec) {
+        cudaError_t e = cudaGraphLaunch(w.exec, w.s);
+        if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); return RB_ECUDA; }
+    } else {
+        for (int k = 0; k < CHECK_EVERY; ++k) enqueue_step(ctx, w.P, w.L, w.o, w.m, w.use_tc);
     }
-    const long long max_steps = (long long)o.max_iter + 2LL * o.max_outer + 64;
-    long long steps = 0;
-    rb_status rs = RB_OK;
-    int copied = 0;   // finished queries whose solution copy to x_host is issued
-    auto copy_finished = [&](int upto) {
-        for (; copied < upto; ++copied) {
-            const int q = ctx->h_done[copied];
-            if (q < 0 || q >= B) continue;
-            cudaMemcpyAsync(x_host + (size_t)q * N, x64 + (size_t)q * N, (size_t)N * sizeof(double),
+    w.steps += CHECK_EVERY;
+    cudaMemcpyAsync(ctx->h_ndone, ctx->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, w.s);
+    cudaMemcpyAsync(ctx->h_err, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, w.s);
+    if (w.x_host) cudaMemcpyAsync(ctx->h_done, ctx->d_done, (size_t)w.B * sizeof(int), cudaMemcpyDeviceToHost, w.s);
+    return RB_OK;
+}
+
+// after wave_launch: wait for the stream, issue the copies of finished solutions, decide
+void wave_check(Wave& w) {
+    rb_ctx* ctx = w.ctx;
+    const long long N = ctx->N;
+    cudaError_t e = cudaStreamSynchronize(w.s);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("solve failed: ") + cudaGetErrorString(e);
+        w.rs = RB_ECUDA;
+        w.finished = true;
+        return;
+    }
+    if (ctx->profiling) flush_profile(ctx);
+    if (*ctx->h_err) {
+        // a kernel gave up waiting on an asynchronous copy: its work items are lost and some
+        // query can no longer finish; stop here (the flag is cleared in wave_end)
+        ctx->err = "a kernel gave up waiting on an asynchronous copy or MMA (device timeout)";
+        w.rs = RB_ETIMEOUT;
+        w.finished = true;
+        return;
+    }
+    if (w.x_host) {
+        const int upto = std::min(*ctx->h_ndone, w.B);
+        for (; w.copied < upto; ++w.copied) {
+            const int q = ctx->h_done[w.copied];
+            if (q < 0 || q >= w.B) continue;
+            cudaMemcpyAsync(w.x_host + (size_t)q * N, w.x64 + (size_t)q * N, (size_t)N * sizeof(double),
                             cudaMemcpyDeviceToHost, ctx->copy_stream);
         }
-    };
-    for (;;) {
-        if (exec) {
-            cudaError_t e = cudaGraphLaunch(exec, s);
-            if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); rs = RB_ECUDA; break; }
-        } else {
-            for (int k = 0; k < check_every; ++k) enqueue_step(ctx, P, L, o, m, use_tc);
-        }
-        steps += check_every;
-        cudaMemcpyAsync(ctx->h_ndone, ctx->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (x_host) cudaMemcpyAsync(ctx->h_done, ctx->d_done, (size_t)B * sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { ctx->err = std::string("solve failed: ") + cudaGetErrorString(e); rs = RB_ECUDA; break; }
-        if (ctx->profiling) flush_profile(ctx);
-        if (x_host) copy_finished(std::min(*ctx->h_ndone, B));
-        if (*ctx->h_ndone >= B) break;
-        if (steps > max_steps) {
-            ctx->err = "solver state machine did not finish within its step budget";
-            rs = RB_ETIMEOUT;
-            break;
-        }
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (x_host) {
+    if (*ctx->h_ndone >= w.B) {
+        w.finished = true;
+        return;
+    }
+    if (w.steps > w.max_steps) {
+        ctx->err = "solver state machine did not finish within its step budget";
+        w.rs = RB_ETIMEOUT;
+        w.finished = true;
+    }
+}
+
+rb_status wave_end(Wave& w, rb_stats* stats) {
+    rb_ctx* ctx = w.ctx;
+    const int B = w.B;
+    cudaStream_t s = w.s;
+    const long long N = ctx->N;
+    rb_status rs = w.rs;
+    if (rs == RB_ETIMEOUT) {
+        cudaStreamSynchronize(s);
+        cudaMemsetAsync(ctx->d_tcerr, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
+    }
+    if (w.x_host) {
         // queries that never reached PH_DONE (a failed wave) still get their current iterate
         if (rs != RB_OK) {
             std::vector<char> seen(B, 0);
-            for (int i = 0; i < copied; ++i)
+            for (int i = 0; i < w.copied; ++i)
                 if (ctx->h_done[i] >= 0 && ctx->h_done[i] < B) seen[ctx->h_done[i]] = 1;
             for (int q = 0; q < B; ++q)
                 if (!seen[q])
-                    cudaMemcpyAsync(x_host + (size_t)q * N, x64 + (size_t)q * N, (size_t)N * sizeof(double),
+                    cudaMemcpyAsync(w.x_host + (size_t)q * N, w.x64 + (size_t)q * N, (size_t)N * sizeof(double),
                                     cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
         }
@@ -731,10 +864,34 @@ rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool 
             stats[q].restarts = st.restarts;
             stats[q].status = st.status;
             stats[q].rel_res = st.rel_res;
+            stats[q].n_used = st.n_used;
         }
         if (st.status > (int)worst) worst = (rb_status)st.status;
     }
     return worst;
+}
+
+// Solve one wave of B <= Bmax queries; x64 is a device array [B][N].  With x_host
+// (host [B][N]) the solution of every query is copied there as soon as the query
+// finishes, on a side stream, while the others still iterate.
+rb_status run_wave(rb_ctx* ctx, int B, const double* mu_host, double* x64, bool x_given, const rb_opts& o, Mode m,
+                   rb_stats* stats, double* x_host) {
+    Wave w;
+    w.ctx = ctx;
+    w.B = B;
+    w.x64 = x64;
+    w.x_host = x_host;
+    w.x_given = x_given;
+    w.o = o;
+    w.m = m;
+    w.s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
+    TRY(wave_begin(w, mu_host));
+    while (!w.finished) {
+        rb_status e = wave_launch(w);
+        if (e != RB_OK) { w.rs = e; break; }
+        wave_check(w);
+    }
+    return wave_end(w, stats);
 }
 
 rb_status run_batch(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts* opts, rb_stats* stats, Mode m) {
@@ -746,7 +903,9 @@ rb_status run_batch(rb_ctx* ctx, int B, const double* mu, double* x, const rb_op
     TRY(validate_opts(ctx, o));
     if (m.rbi) m.mixed = false;
     else m.mixed = o.precision == RB_PREC_MIXED;
-    const bool dev_x = is_device_ptr(x);
+    bool bad = false;
+    const bool dev_x = is_device_ptr(ctx, x, &bad);
+    if (bad) return RB_EINVAL;
     const bool x_given = o.x0_mode == RB_X0_GIVEN;
     cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->own_stream;
     const long long N = ctx->N;
@@ -787,6 +946,8 @@ void rb_default_opts(rb_opts* o) {
     o->graph = 1;
     o->kernels = 0;
     o->store = RB_STORE_F32;
+    o->adaptive_n = 0;
+    o->gamma = 10.0;
     o->stream = nullptr;
 }
 
@@ -837,6 +998,17 @@ rb_status rb_offline_load_arrays(rb_ctx** out, const rb_problem* prob, int n, co
         return s;
     }
     *out = ctx;
+    return RB_OK;
+}
+
+rb_status rb_debug_wait(rb_ctx* ctx, double limit_s, long long skip_stage) {
+    if (!ctx) return RB_EINVAL;
+    if (!(limit_s > 0.0) || !(limit_s <= 2.0) || skip_stage < -1) {
+        ctx->err = "need 0 < limit_s <= 2 and skip_stage >= -1";
+        return RB_EINVAL;
+    }
+    ctx->wait_ns = (unsigned long long)(limit_s * 1e9);
+    ctx->dbg_skip = skip_stage;
     return RB_OK;
 }
 
@@ -897,6 +1069,7 @@ rb_status rb_products(rb_ctx* ctx, int B, const float* R, double* WtR, const flo
     for (int q = 0; q < B; ++q) {
         std::memset(&ctx->h_st[q], 0, sizeof(QState));
         ctx->h_st[q].phase = PH_PREC;
+        ctx->h_st[q].n_used = n;
     }
     CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
     std::vector<int> lc(N_LISTS, 0), li(B);
@@ -964,6 +1137,7 @@ rb_status rb_precondition(rb_ctx* ctx, int B, const double* mu, const void* r, v
         std::memset(&ctx->h_st[q], 0, sizeof(QState));
         ctx->h_st[q].phase = PH_PREC;
         ctx->h_st[q].start = 1;
+        ctx->h_st[q].n_used = first_n_used(ctx, o, m);
     }
     CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
     std::vector<int> lc(N_LISTS, 0), li(B);
@@ -1049,9 +1223,10 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
         if (best.smoother == RB_SMOOTH_RBGS && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
             !ctx->force_generic) {
             const rb_opts base = best;
-            for (int kk = 0; kk <= 2; ++kk) {
+            for (int kk = 0; kk <= 3; ++kk) {
                 if (kk == base.kernels || (kk == 1 && ctx->geo.dim == 2 && !use_fused_smoother(ctx->geo, base.nu)))
                     continue;
+                if (kk == 3 && (ctx->geo.dim != 2 || !use_multi_smoother(ctx->geo))) continue;
                 if (kk != 0 && base.store == RB_STORE_BF16) continue;   // BF16 iterates need kernels = 0
                 rb_opts t = base;
                 t.kernels = kk;
@@ -1084,12 +1259,76 @@ rb_status rb_pcg(rb_ctx* ctx, int B, const double* mu, double* x, const rb_opts*
     return run_batch(ctx, B, mu, x, opts, stats, Mode{false, false});
 }
 
+rb_status rb_pcg_ragged(rb_ctx* const* ctxs, int nctx, const int* B, const double* const* mu, double* const* x,
+                        const rb_opts* opts, rb_stats* const* stats) {
+    if (!ctxs || !B || !mu || !x || nctx < 1 || nctx > 16) {
+        g_create_error = "rb_pcg_ragged needs 1..16 contexts and their B, mu and x";
+        return RB_EINVAL;
+    }
+    rb_opts o;
+    rb_default_opts(&o);
+    if (opts) o = *opts;
+    std::vector<Wave> waves(nctx);
+    for (int c = 0; c < nctx; ++c) {
+        rb_ctx* ctx = ctxs[c];
+        if (!ctx) { g_create_error = "a context is NULL"; return RB_EINVAL; }
+        for (int d = 0; d < c; ++d)
+            if (ctxs[d] == ctx) { g_create_error = "a context appears twice"; return RB_EINVAL; }
+        TRY(validate_opts(ctx, o));
+        if (B[c] < 0 || B[c] > ctx->Bmax || (B[c] > 0 && (!mu[c] || !x[c]))) {
+            ctx->err = "need 0 <= B <= max_batch of the context and non-NULL mu, x";
+            return RB_EINVAL;
+        }
+        bool bad = false;
+        if (B[c] > 0 && !is_device_ptr(ctx, x[c], &bad)) {
+            if (!bad) ctx->err = "rb_pcg_ragged needs x in device memory";
+            return RB_EINVAL;
+        }
+        Wave& w = waves[c];
+        w.ctx = ctx;
+        w.B = B[c];
+        w.x64 = x[c];
+        w.x_given = o.x0_mode == RB_X0_GIVEN;
+        w.o = o;
+        w.o.stream = nullptr;   // every context advances on its own stream
+        w.m = Mode{false, o.precision == RB_PREC_MIXED};
+        w.s = ctx->own_stream;
+        w.finished = B[c] == 0;
+    }
+    // every context's setup, then one launch sequence: each round enqueues CHECK_EVERY steps of
+    // every unfinished context on its own stream (the kernels of the contexts run side by
+    // side on the GPU), then polls them all
+    if (o.stream) CK_GLOBAL(cudaStreamSynchronize((cudaStream_t)o.stream));
+    for (int c = 0; c < nctx; ++c)
+        if (!waves[c].finished) TRY(wave_begin(waves[c], mu[c]));
+    for (;;) {
+        bool any = false;
+        for (Wave& w : waves)
+            if (!w.finished) {
+                rb_status e = wave_launch(w);
+                if (e != RB_OK) { w.rs = e; w.finished = true; }
+                any = true;
+            }
+        if (!any) break;
+        for (Wave& w : waves)
+            if (!w.finished) wave_check(w);
+    }
+    rb_status worst = RB_OK;
+    for (int c = 0; c < nctx; ++c) {
+        rb_status r = B[c] > 0 ? wave_end(waves[c], stats ? stats[c] : nullptr) : RB_OK;
+        if (r > worst) worst = r;
+    }
+    return worst;
+}
+
 rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double* y, void* stream) {
     if (!ctx) return RB_EINVAL;
     if (B < 0 || (B > 0 && (!mu || !x || !y))) { ctx->err = "B < 0 or NULL argument"; return RB_EINVAL; }
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
     const long long N = ctx->N;
-    const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+    bool bad = false;
+    const bool dx = is_device_ptr(ctx, x, &bad), dy = is_device_ptr(ctx, y, &bad);
+    if (bad) return RB_EINVAL;
     for (int b0 = 0; b0 < B; b0 += ctx->Bmax) {
         const int nbw = std::min(ctx->Bmax, B - b0);
         for (size_t i = 0; i < (size_t)nbw * ctx->n_mu; ++i)
@@ -1116,7 +1355,7 @@ rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, doubl
         return RB_EINVAL;
     }
     if (net && !mlp_ready(net)) { ctx->err = "the network has not been fitted"; return RB_EINVAL; }
-    if (is_device_ptr(mu)) { ctx->err = "mu must be host memory"; return RB_EINVAL; }
+    if (pointer_kind(mu) != PTR_HOST) { ctx->err = "mu must be host memory"; return RB_EINVAL; }
     for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i) {
         if (!std::isfinite(mu[i]) || ((int)(i % ctx->n_mu) < ctx->P && !(mu[i] > 0.0))) {
             ctx->err = "parameter vectors must be finite, with positive diffusion coefficients";
@@ -1126,7 +1365,9 @@ rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, doubl
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
     const long long N = ctx->N;
     const int n = ctx->n;
-    const bool dx = is_device_ptr(x), dc = coef && is_device_ptr(coef);
+    bool bad = false;
+    const bool dx = is_device_ptr(ctx, x, &bad), dc = coef && is_device_ptr(ctx, coef, &bad);
+    if (bad) return RB_EINVAL;
     LoadMap lm{};
     for (int r = 0; r < ctx->R; ++r) lm.param[r] = ctx->load_param[r];
     const int chunk = std::max(1, std::min<int>(ctx->Bmax, (int)(ctx->scratch_bytes / sizeof(double)) / std::max(1, n)));
@@ -1153,10 +1394,10 @@ rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, doubl
             CK(cudaMemcpyAsync(coef + (size_t)b0 * n, c, (size_t)nbw * n * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
-    int bad = 0;
-    CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int notspd = 0;
+    CK(cudaMemcpyAsync(&notspd, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (bad) { ctx->err = "A_N(mu) is not positive definite for some query"; return RB_EBREAKDOWN; }
+    if (notspd) { ctx->err = "A_N(mu) is not positive definite for some query"; return RB_EBREAKDOWN; }
     return RB_OK;
 }
 
@@ -1167,7 +1408,9 @@ rb_status rb_coefficients(rb_ctx* ctx, int B, const double* x, double* coef, voi
     const long long N = ctx->N;
     const int n = ctx->n;
     if (n == 0 || B == 0) return RB_OK;
-    const bool dx = is_device_ptr(x), dc = is_device_ptr(coef);
+    bool bad = false;
+    const bool dx = is_device_ptr(ctx, x, &bad), dc = is_device_ptr(ctx, coef, &bad);
+    if (bad) return RB_EINVAL;
     const size_t sd = ctx->scratch_bytes / sizeof(double);
     int chunk = std::min(ctx->Bmax, 256);
     while (chunk > 1 && (size_t)coef_splits(chunk, ctx->num_sms) * chunk * n > sd) chunk /= 2;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
             if (!producer) {
                 const T* sg = ring + (size_t)cslot * lay.stage_elems + lay.pad;
                 const T* sprev = ring + (size_t)(cslot == 0 ? RING - 1 : cslot - 1) * lay.stage_elems + lay.pad;
-                if (ok && !mb_wait(bar + cslot, cpar, P.err)) ok = false;
+                if (ok && !mb_wait(bar + cslot, cpar, P.err, P.wait_ns)) ok = false;
                 V4t<T> a = lds4(sg + x0);
                 if (use_old) {
                     const V4t<T> b = lds4(sg + lay.stride + x0);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_a(Params P) {
             }
         }
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, cur.issued);
+            if (issuer) drain(bar, cur.issued, P.wait_ns);
             __syncthreads();
             return;
         }
@@ -228,6 +228,11 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
         uint64_t* b = bar + u % RING;
         const int kk = cur.k, m = kk + 1;
         const bool rows_rd = kk >= cur.y0;   // r and d rows of the band (kk < y1 always)
+        if (P.dbg_skip >= 0 && blockIdx.x == 0 && (long long)u == P.dbg_skip) {
+            // test hook: this stage is never issued, so the consumers' bounded wait on it runs out
+            if (++cur.k > cur.y1 - 1) cursor_item(cur.w + gridDim.x);
+            return;
+        }
         mb_arrive_tx(b, row_bytes * (rows_rd ? 3u : 1u));
         bulk_row(sg, (m >= 0 && m < my) ? cur.pg + (size_t)m * mx : zero_row, row_bytes, b);
         if (rows_rd) {
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
             if (!producer) {
                 const T* sg = ring + (size_t)cslot * lay.stage_elems + lay.pad;
                 const T* sprev = ring + (size_t)(cslot == 0 ? RING - 1 : cslot - 1) * lay.stage_elems + lay.pad;
-                if (ok && !mb_wait(bar + cslot, cpar, P.err)) ok = false;
+                if (ok && !mb_wait(bar + cslot, cpar, P.err, P.wait_ns)) ok = false;
                 const V4t<T> a = lds4(sg + x0);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_cg_b(Params P) {
             }
         }
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, cur.issued);
+            if (issuer) drain(bar, cur.issued, P.wait_ns);
             __syncthreads();
             return;
         }

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/rb.h"
 
 namespace rbk {
@@ -60,7 +62,7 @@ struct QState {
     int phase;
     int start;           // 1: the next preconditioner output starts a CG cycle (beta = 0)
     int ppar;            // current half of the p ping-pong buffer
-    int rpar_unused;
+    int n_used;          // basis vectors of the next preconditioner application (adaptive N)
     int xzero;           // x is exactly zero (skip A x in the residual)
     int pad_;
 };
@@ -79,7 +81,8 @@ struct Params {
     int nb, nbp;                 // basis size and padded stride
     const double* W64c;
     const float* W32c;
-    const double* L;             // [Bmax][nbp][nbp] A_N(mu)^{-1} (row-major, formed from the Cholesky factor)
+    const double* L;             // [Bmax][nbp][nbp] A_N(mu)^{-1} (row-major, formed from the Cholesky factor);
+                                 // with adaptive N the inverse factor X = L^{-1} + L^{-T} - diag(L^{-1})
     // vectors
     double* x64;                 // [B][N] FP64 iterate / solution
     void* r;                     // [B][N] of T (updated in place)
@@ -109,6 +112,11 @@ struct Params {
     double omega;
     int mixed;                   // 1: T = float inner with FP64 refinement
     int ybf16;                   // 1: the smoother's iterates (ypro, tmp) are stored as BF16
+    int adaptive;                // 1: N grows per query (end of Section 4.1); QState.n_used
+    double gamma;                // residual-ratio threshold of the growth test
+    unsigned long long wait_ns;  // limit of every bounded wait on an asynchronous copy
+    long long dbg_skip;          // test hook (rb_debug_wait): the staged CG part-B producer of CTA 0
+                                 // leaves this stage unissued (-1: never)
 };
 
 // ----------------------------------------------------------------------------
@@ -262,16 +270,21 @@ __device__ __forceinline__ void finalize_cg_a_state(const Params& P, int q, doub
 __device__ __forceinline__ void finalize_cg_b_state(const Params& P, int q, double rr) {
     QState& s = P.st[q];
     const double rn = sqrt(rr);
-    s.rnorm = rn;
     s.iters += 1;
     if (!(rn == rn)) {
+        s.rnorm = rn;
         mark_done(P, s, RB_EBREAKDOWN);
         return;
     }
     if (rn < s.target || s.iters >= P.max_iter) {
+        s.rnorm = rn;
         s.phase = PH_OUTER;
         list_push(P, L_OUT, q);
     } else {
+        // adaptive N (end of Section 4.1): a residual that fell by less than gamma in this
+        // iteration, ||r_k|| / ||r_{k+1}|| < gamma, adds one basis vector to the next application
+        if (P.adaptive && s.n_used < P.nb && s.rnorm < P.gamma * rn) s.n_used += 1;
+        s.rnorm = rn;
         s.phase = PH_PREC;
         list_push(P, L_PREC, q);
     }
@@ -336,6 +349,10 @@ template <typename T> void launch2d_cg_b_staged(const Params& P, const Launch& L
 // one sweep per launch with rows staged in shared memory by bulk asynchronous copies
 bool use_tma_smoother(const Geo& g);
 template <typename T> void launch2d_smooth_tma(const Params& P, const Launch& L, int nu);
+// nu sweeps in passes of up to three, rows staged by bulk asynchronous copies (FP32, dim 2,
+// rows of a multiple of 128 points)
+bool use_multi_smoother(const Geo& g);
+void launch2d_smooth_multi(const Params& P, const Launch& L, int nu);
 // all nu sweeps in one pass (FP32, dim 2, mx even, nu <= 6)
 bool use_fused_smoother(const Geo& g, int nu);
 void launch2d_smooth_fused(const Params& P, const Launch& L, int nu);
@@ -347,6 +364,12 @@ template <typename T> void launch3d_smooth(const Params& P, const Launch& L, int
 template <typename T> void launch3d_smooth_staged(const Params& P, const Launch& L, int nu);
 template <typename T> void launch3d_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch3d_cg_b(const Params& P, const Launch& L);
+// 3D kernels marching in z over tiles of whole x-rows (rows of a multiple of 4 points, at most
+// 256): 4 points per thread, planes staged by bulk row copies, one CTA barrier per plane
+bool use_ztile(const Geo& g, bool fp64);
+// (false: a tensor map could not be encoded; nothing was launched)
+template <typename T> bool launch3d_cg_tile(const Params& P, const Launch& L, bool part_a);
+template <typename T> bool launch3d_smooth_tile(const Params& P, const Launch& L, int nu);
 template <typename T> void launch_cg_a(const Params& P, const Launch& L);
 template <typename T> void launch_cg_b(const Params& P, const Launch& L);
 void launch_rbi_residual(const Params& P, const Launch& L);
@@ -384,5 +407,13 @@ rb_status mlp_predict_device(rb_mlp* net, int B, const double* d_mu, int ld_mu, 
 
 int tiles_flat(long long n);
 int tiles_box(const Geo& g);
+
+// Where a caller's buffer lives.  Device memory of another GPU is rejected by
+// every call: a kernel of this device cannot read it without peer access.
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+PtrKind pointer_kind(const void* p);   // managed memory counts as PTR_DEVICE
+
+// Checks of an rb_problem shared by every entry point that takes one (rb_api.cu).
+rb_status validate_problem(const rb_problem* prob, std::string& why);
 
 }  // namespace rbk

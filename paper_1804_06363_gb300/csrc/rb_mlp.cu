@@ -356,15 +356,7 @@ __global__ void k_mlp_round(long long np, const float* w, __nv_bfloat16* wb) {
         wb[p] = __float2bfloat16_rn(w[p]);
 }
 
-bool is_dev(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool is_dev(const void* p) { return rbk::pointer_kind(p) == rbk::PTR_DEVICE; }
 
 }  // namespace
 
@@ -449,7 +441,7 @@ rb_status check_mu(const rb_mlp* n, int B, const double* mu) {
 // Stage S training pairs on the device; the first call also fixes the standardisation.
 rb_status stage_pairs(rb_mlp* n, int S, const double* mu, const double* Y, cudaStream_t s) {
     if (S < 1 || S > n->Smax || !mu || !Y) return fail(RB_EINVAL, "need 1 <= S <= max_samples and non-NULL mu, Y");
-    if (is_dev(mu)) return fail(RB_EINVAL, "mu must be host memory");
+    if (rbk::pointer_kind(mu) != rbk::PTR_HOST) return fail(RB_EINVAL, "mu must be host memory");
     if (check_mu(n, S, mu) != RB_OK) return RB_EINVAL;
     MCK(cudaMemcpyAsync(n->d_mu, mu, (size_t)S * n->I * sizeof(double), cudaMemcpyHostToDevice, s));
     MCK(cudaMemcpyAsync(n->d_tgt, Y, (size_t)S * n->O * sizeof(double), cudaMemcpyDefault, s));
@@ -611,8 +603,9 @@ rb_status rb_mlp_predict(rb_mlp* n, int B, const double* mu, double* Y, void* st
     if (!n) return fail(RB_EINVAL, "network is NULL");
     if (B < 0 || (B > 0 && (!mu || !Y))) return fail(RB_EINVAL, "B < 0 or NULL mu / Y");
     if (!n->scaled) return fail(RB_EINVAL, "the network has no standardisation yet: fit it first");
-    if (is_dev(mu)) return fail(RB_EINVAL, "mu must be host memory");
+    if (rbk::pointer_kind(mu) != rbk::PTR_HOST) return fail(RB_EINVAL, "mu must be host memory");
     if (check_mu(n, B, mu) != RB_OK) return RB_EINVAL;
+    if (rbk::pointer_kind(Y) == rbk::PTR_OTHER_DEVICE) return fail(RB_EINVAL, "Y lives on another device");
     cudaStream_t s = stream ? (cudaStream_t)stream : n->own;
     const bool dev_y = is_dev(Y);
     for (int b0 = 0; b0 < B; b0 += n->Smax) {

@@ -15,6 +15,7 @@
 // the scratch instead of a context workspace, then one warp per query adds
 // them in a fixed order.  Block indices and load terms are computed on the
 // fly, so no table of the context is needed either.
+#include <cuda.h>   // driver types only (entry points are looked up through the runtime)
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -40,7 +41,12 @@ constexpr int NA_MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_na_scratch[NA_SCRATCH_BYTES];
 
 std::mutex g_na_mutex;
-void* g_na_addr[NA_MAX_DEVICES] = {nullptr};
+// per device: the CUDA context the address was looked up in (its process-unique id) and the address
+struct NaSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
+NaSlot g_na_slot[NA_MAX_DEVICES] = {};
 
 // error text is reported through rb_last_error(NULL)
 struct NaError {
@@ -157,23 +163,56 @@ __global__ void k_na_finish(int B, int ntiles, const double* part, double* out) 
 
 size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Id of the current CUDA context (0 when it cannot be had).  A device reset, or a release and
+// re-creation of the primary context, reloads the module, and the scratch array may then live at
+// another address; the id tells the two contexts apart.  The driver entry points are looked up
+// through the runtime, so the library needs no link to libcuda.
+unsigned long long na_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the scratch array on the current device, looked up with that device
+// current on the first call in each context (once per device unless the device is reset).
 rb_status na_scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { g_na_error = cudaGetErrorString(e); return RB_ECUDA; }
     if (dev < 0 || dev >= NA_MAX_DEVICES) { g_na_error = "device index out of range"; return RB_EINVAL; }
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
+    NaSlot& slot = g_na_slot[dev];
+    const unsigned long long id = na_context_id();
+    if (!slot.addr || id == 0 || id != slot.ctx_id) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess || !p) {
             g_na_error = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
             return RB_ECUDA;
         }
-        g_na_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx_id = na_context_id();   // the lookup has made the context current if it was not
     }
-    *out = g_na_addr[dev];
+    *out = slot.addr;
     return RB_OK;
 }
 
@@ -182,28 +221,17 @@ rb_status na_scratch_address(void** out) {
 extern "C" rb_status rb_residual_noalloc(const rb_problem* prob, int B, const double* mu, const double* x,
                                          double* rel_res, void* stream) {
     g_na_error.clear();
-    if (!prob || B < 0 || (B > 0 && (!mu || !x || !rel_res))) { g_na_error = "NULL argument or B < 0"; return RB_EINVAL; }
-    if (prob->dim != 2 && prob->dim != 3) { g_na_error = "dim must be 2 or 3"; return RB_EINVAL; }
-    long long P = 1, n = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (prob->m[d] < 1 || prob->nb[d] < 1 || prob->nb[d] > prob->m[d]) { g_na_error = "bad grid / blocks"; return RB_EINVAL; }
-        P *= prob->nb[d];
-        n *= prob->m[d];
-    }
-    if (prob->dim == 2 && (prob->m[2] != 1 || prob->nb[2] != 1)) { g_na_error = "dim 2 needs m[2] = nb[2] = 1"; return RB_EINVAL; }
-    if (n >= (1LL << 31) || P > rbk::MAX_P || prob->n_mu < P || prob->n_mu > rbk::MAX_MU ||
-        prob->n_loads < 1 || prob->n_loads > rbk::MAX_LOADS || !prob->loads) {
-        g_na_error = "problem out of range";
-        return RB_EINVAL;
-    }
+    if (B < 0 || (B > 0 && (!mu || !x || !rel_res))) { g_na_error = "NULL argument or B < 0"; return RB_EINVAL; }
+    std::string why;
+    if (rbk::validate_problem(prob, why) != RB_OK) { g_na_error = why; return RB_EINVAL; }
+    const long long n = (long long)prob->m[0] * prob->m[1] * prob->m[2];
     if (B == 0) return RB_OK;
     for (size_t i = 0; i < (size_t)B * prob->n_mu; ++i)
         if (!std::isfinite(mu[i])) { g_na_error = "non-finite parameter"; return RB_EINVAL; }
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, x) != cudaSuccess ||
-        (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        g_na_error = "x must be device memory";
+    const rbk::PtrKind xk = rbk::pointer_kind(x);
+    if (xk != rbk::PTR_DEVICE) {
+        g_na_error = xk == rbk::PTR_OTHER_DEVICE ? "x lives on another device than the current one"
+                                                 : "x must be device memory";
         return RB_EINVAL;
     }
     const int ntiles = (int)((n + NA_TILE - 1) / NA_TILE);
@@ -235,10 +263,6 @@ extern "C" rb_status rb_residual_noalloc(const rb_problem* prob, int B, const do
     g.ihz2 = g.dim == 3 ? (double)(g.mz + 1) * (g.mz + 1) : 0.0;
     for (int r = 0; r < g.R; ++r) {
         const rb_load& l = prob->loads[r];
-        if ((l.kind != RB_LOAD_CONST && l.kind != RB_LOAD_GAUSS) || l.param < -1 || l.param >= prob->n_mu) {
-            g_na_error = "bad load term";
-            return RB_EINVAL;
-        }
         g.kind[r] = l.kind;
         g.param[r] = l.param;
         g.cx[r] = l.center[0]; g.cy[r] = l.center[1]; g.cz[r] = l.center[2];

@@ -58,7 +58,9 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
     rb_opts o = so;
     o.tol = b.truth_tol;
     o.max_iter = b.truth_max_iter;
-    o.precision = RB_PREC_FP64;
+    // snapshots in the precision the caller asks for: FP64, or FP32 inner RBCG with FP64
+    // residual refinement (the snapshot still reaches the FP64 relative residual truth_tol)
+    const Mode snap_mode{false, so.precision == RB_PREC_MIXED};
     o.x0_mode = RB_X0_ZERO;
     o.stream = nullptr;
     o.max_outer = std::max(o.max_outer, 40);
@@ -76,7 +78,7 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
         const int n = ctx->n;
         // step 3: snapshot, RBCG with W_{n} (no basis when n = 0)
         rb_stats st;
-        rb_status ws = run_wave(ctx, 1, mu_train + (size_t)cand * n_mu, bb.snap, false, o, Mode{false, false}, &st, nullptr);
+        rb_status ws = run_wave(ctx, 1, mu_train + (size_t)cand * n_mu, bb.snap, false, o, snap_mode, &st, nullptr);
         // a snapshot that stalled at the FP64 residual floor within 10x the target is kept
         if (ws == RB_ENOCONV && st.rel_res < 10.0 * b.truth_tol) ws = RB_OK;
         if (ws != RB_OK) {

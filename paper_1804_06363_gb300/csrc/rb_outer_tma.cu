@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
                     const double* sg = ring + (size_t)cslot * lay.stage_elems + lay.pad;
                     const double* sprev =
                         ring + (size_t)(cslot == 0 ? RING - 1 : cslot - 1) * lay.stage_elems + lay.pad;
-                    if (ok && !mb_wait(bar + cslot, cpar, P.err)) ok = false;
+                    if (ok && !mb_wait(bar + cslot, cpar, P.err, P.wait_ns)) ok = false;
                     const V4t<double> a = lds4(sg + x0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2s_outer_residual(Params P) 
             }
         }
         if (__syncthreads_or(!ok)) {
-            if (issuer) drain(bar, cur.issued);
+            if (issuer) drain(bar, cur.issued, P.wait_ns);
             __syncthreads();
             return;
         }

@@ -106,20 +106,53 @@ __global__ void __launch_bounds__(THREADS) k_reduced_solve(Params P) {
         double acc[MAX_N / 32];
 #pragma unroll
         for (int t = 0; t < MAX_N / 32; ++t) acc[t] = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            const double vj = v[j];
-            const double* row = Ai + (size_t)j * nbp;
+        int nu_ = nb;   // basis vectors used by this application
+        if (P.adaptive) {
+            // e = M_k^T (M_k v_k) with the inverse factor M stored as X (k_cholesky):
+            // z_i = sum_{j <= i} X[j][i] v_j, then e_j = sum_{i >= j} X[i][j] z_i, i, j < k
+            nu_ = P.st[q].n_used;
+            for (int j = 0; j < nu_; ++j) {
+                const double vj = v[j];
+                const double* row = Ai + (size_t)j * nbp;
+#pragma unroll
+                for (int t = 0; t < MAX_N / 32; ++t) {
+                    const int k = lane + 32 * t;
+                    if (k >= j && k < nu_) acc[t] += row[k] * vj;
+                }
+            }
+            __syncwarp();
 #pragma unroll
             for (int t = 0; t < MAX_N / 32; ++t) {
                 const int k = lane + 32 * t;
-                if (k < nb) acc[t] += row[k] * vj;
+                if (k < nu_) v[k] = acc[t];
+                acc[t] = 0.0;
+            }
+            __syncwarp();
+            for (int i = 0; i < nu_; ++i) {
+                const double zi = v[i];
+                const double* row = Ai + (size_t)i * nbp;
+#pragma unroll
+                for (int t = 0; t < MAX_N / 32; ++t) {
+                    const int k = lane + 32 * t;
+                    if (k <= i) acc[t] += row[k] * zi;
+                }
+            }
+        } else {
+            for (int j = 0; j < nb; ++j) {
+                const double vj = v[j];
+                const double* row = Ai + (size_t)j * nbp;
+#pragma unroll
+                for (int t = 0; t < MAX_N / 32; ++t) {
+                    const int k = lane + 32 * t;
+                    if (k < nb) acc[t] += row[k] * vj;
+                }
             }
         }
         T* e = reinterpret_cast<T*>(P.e) + (size_t)q * P.lde;
 #pragma unroll
         for (int t = 0; t < MAX_N / 32; ++t) {
             const int k = lane + 32 * t;
-            if (k < P.lde) e[k] = k < nb ? (T)acc[t] : T(0);
+            if (k < P.lde) e[k] = k < nu_ ? (T)acc[t] : T(0);
         }
         __syncwarp();
     }
@@ -239,7 +272,23 @@ __global__ void __launch_bounds__(THREADS) k_cholesky(Params P, const double* __
     // A_N^{-1} = L^{-T} L^{-1}, column j by the two triangular solves L z = e_j,
     // L^T x = z (thread j owns column j of the output; the output doubles as z)
     double* Ai = const_cast<double*>(P.L) + (size_t)q * nbp * nbp;
-    if (!bad) {
+    if (!bad && P.adaptive) {
+        // adaptive N: the inverse factor M = L^{-1}, stored as X = M + M^T - diag(M).  The
+        // leading k x k block of M is the inverse factor of the leading block of A_N (W_k is
+        // nested in W_N), so one X serves every N <= nb: e = M_k^T (M_k r_k).
+        for (int j = threadIdx.x; j < nb; j += THREADS) {
+            for (int i = 0; i < nb; ++i) {
+                double sacc = (i == j) ? 1.0 : 0.0;
+                for (int k = j; k < i; ++k) sacc -= A[i * nb + k] * Ai[(size_t)k * nbp + j];
+                if (i >= j) Ai[(size_t)i * nbp + j] = sacc / A[i * nb + i];
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nb * nb; idx += THREADS) {
+            const int i = idx / nb, j = idx % nb;
+            if (j > i) Ai[(size_t)i * nbp + j] = Ai[(size_t)j * nbp + i];
+        }
+    } else if (!bad) {
         for (int j = threadIdx.x; j < nb; j += THREADS) {
             for (int i = 0; i < nb; ++i) {
                 double sacc = (i == j) ? 1.0 : 0.0;

@@ -109,7 +109,7 @@ __device__ __noinline__ void smooth_producer(const Params& P, const S* __restric
         const int y0 = band * rows, y1 = min(my, y0 + rows);
         for (int kk = y0 - 3; kk <= y1; ++kk, ++u) {
             const unsigned i = u % RING;
-            if (u >= (unsigned)RING && !mb_wait(empty + i, ((u / RING) + 1) & 1u, P.err)) {
+            if (u >= (unsigned)RING && !mb_wait(empty + i, ((u / RING) + 1) & 1u, P.err, P.wait_ns)) {
                 ok = false;
                 break;
             }
@@ -126,7 +126,7 @@ __device__ __noinline__ void smooth_producer(const Params& P, const S* __restric
                          row_bytes, full + i);
         }
     }
-    drain(full, u);   // copies still in flight (only after an expired wait do any remain)
+    drain(full, u, P.wait_ns);   // copies still in flight (only after an expired wait do any remain)
 }
 
 // S: storage of the source rows (and of dst unless LAST); dst of the last sweep is T.
@@ -227,7 +227,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 96 : 168) k2_smooth_tma(Params P, c
             constexpr int PAR = decltype(par_tag)::value;
             constexpr int R0 = PAR, R1 = PAR + 2;   // red columns of row k = black columns of row k-1
             {
-                if (ok && !mb_wait(full + cslot, cpar, P.err)) ok = false;
+                if (ok && !mb_wait(full + cslot, cpar, P.err, P.wait_ns)) ok = false;
                 // source row k+1 at the red columns of row k (its black points)
                 const V4t<T> sn = ld_s4(o_cur + sx0);
                 sbm[0] = sbc[0];

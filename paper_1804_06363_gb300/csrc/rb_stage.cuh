@@ -64,19 +64,19 @@ __device__ __forceinline__ bool mb_test(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false (and the error flag raised) on expiry
-static __device__ __noinline__ bool mb_wait_slow(uint64_t* b, uint32_t parity, int* err) {
+// bounded wait (limit_ns of globaltimer); false (and the error flag raised) on expiry
+static __device__ __noinline__ bool mb_wait_slow(uint64_t* b, uint32_t parity, int* err, unsigned long long limit_ns) {
     const uint64_t t0 = gtime();
     while (!mb_test(b, parity)) {
-        if (gtime() - t0 > WAIT_NS) {
+        if (gtime() - t0 > limit_ns) {
             atomicExch(err, 1);
             return false;
         }
     }
     return true;
 }
-__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, int* err) {
-    return mb_test(b, parity) || mb_wait_slow(b, parity, err);
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, int* err, unsigned long long limit_ns = WAIT_NS) {
+    return mb_test(b, parity) || mb_wait_slow(b, parity, err, limit_ns);
 }
 __device__ __forceinline__ void bulk_row(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -84,11 +84,23 @@ __device__ __forceinline__ void bulk_row(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(s2u(bar))
         : "memory");
 }
-// After an expired wait: let the copies of the last RING stages land (bounded in time).
-__device__ __forceinline__ void drain(uint64_t* bar, unsigned seq) {
+// After an expired wait: let the copies of the last RING stages land (bounded in time:
+// the drain limit, or the wait limit when that is shorter).
+__device__ __forceinline__ void drain(uint64_t* bar, unsigned seq, unsigned long long limit_ns = DRAIN_NS) {
     const uint64_t t0 = gtime();
+    const unsigned long long lim = limit_ns < DRAIN_NS ? limit_ns : DRAIN_NS;
     for (unsigned u = seq > (unsigned)RING ? seq - RING : 0u; u < seq; ++u)
-        while (!mb_test(bar + u % RING, (u / RING) & 1u) && gtime() - t0 < DRAIN_NS) {
+        while (!mb_test(bar + u % RING, (u / RING) & 1u) && gtime() - t0 < lim) {
+        }
+}
+
+// The same for a ring of `ring` stages (kernels whose ring is not RING).
+__device__ __forceinline__ void drain_ring(uint64_t* bar, unsigned seq, unsigned ring,
+                                           unsigned long long limit_ns = DRAIN_NS) {
+    const uint64_t t0 = gtime();
+    const unsigned long long lim = limit_ns < DRAIN_NS ? limit_ns : DRAIN_NS;
+    for (unsigned u = seq > ring ? seq - ring : 0u; u < seq; ++u)
+        while (!mb_test(bar + u % ring, (u / ring) & 1u) && gtime() - t0 < lim) {
         }
 }
 

@@ -533,6 +533,7 @@ bool use_zmarch_smoother(const Geo& g) { return g.dim == 3 && tiles3(g) <= tiles
 
 template <typename T>
 void launch3d_smooth_staged(const Params& P, const Launch& L, int nu) {
+    if (use_ztile(P.g, sizeof(T) == 8) && launch3d_smooth_tile<T>(P, L, nu)) return;
     static bool configured = false;
     const size_t sm = sizeof(SmoothSmem<T>);
     if (!configured) {
@@ -558,6 +559,7 @@ template void launch3d_smooth_staged<double>(const Params&, const Launch&, int);
 
 template <typename T>
 void launch3d_cg_a(const Params& P, const Launch& L) {
+    if (use_ztile(P.g, sizeof(T) == 8) && launch3d_cg_tile<T>(P, L, true)) return;
     static bool configured = false;
     if (!configured) {
         allow_smem(k3s_cg<T, true>, sizeof(CgSmem<T>));
@@ -567,6 +569,7 @@ void launch3d_cg_a(const Params& P, const Launch& L) {
 }
 template <typename T>
 void launch3d_cg_b(const Params& P, const Launch& L) {
+    if (use_ztile(P.g, sizeof(T) == 8) && launch3d_cg_tile<T>(P, L, false)) return;
     static bool configured = false;
     if (!configured) {
         allow_smem(k3s_cg<T, false>, sizeof(CgSmem<T>));

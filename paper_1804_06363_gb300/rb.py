@@ -38,12 +38,13 @@ class RbOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("smoother", C.c_int), ("nu", C.c_int),
                 ("omega", C.c_double), ("precision", C.c_int), ("beta_form", C.c_int), ("x0_mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("gemm", C.c_int), ("graph", C.c_int),
-                ("kernels", C.c_int), ("store", C.c_int), ("stream", C.c_void_p)]
+                ("kernels", C.c_int), ("store", C.c_int), ("adaptive_n", C.c_int), ("gamma", C.c_double),
+                ("stream", C.c_void_p)]
 
 
 class RbStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
-                ("rel_res", C.c_double)]
+                ("rel_res", C.c_double), ("n_used", C.c_int)]
 
 
 class RbBuildOpts(C.Structure):
@@ -72,11 +73,14 @@ SIGNATURES = {
                                    C.POINTER(RbBuildOpts), C.POINTER(RbOpts), C.c_int]),
     "rb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "rb_offline_load": (C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_int]),
+    "rb_debug_wait": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong]),
     "rb_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int),
                           C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rb_get_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
     "rb_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(RbOpts), C.c_void_p]),
+    "rb_pcg_ragged": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(RbOpts),
+                                C.c_void_p]),
     "rb_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_products": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "rb_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(RbOpts)]),
@@ -197,9 +201,9 @@ def make_opts(**kw) -> RbOpts:
 def stats_array(st) -> np.ndarray:
     n = len(st)
     out = np.zeros(n, dtype=[("iters", "i4"), ("outer", "i4"), ("restarts", "i4"), ("status", "i4"),
-                             ("rel_res", "f8")])
+                             ("rel_res", "f8"), ("n_used", "i4")])
     for i in range(n):
-        out[i] = (st[i].iters, st[i].outer, st[i].restarts, st[i].status, st[i].rel_res)
+        out[i] = (st[i].iters, st[i].outer, st[i].restarts, st[i].status, st[i].rel_res, st[i].n_used)
     return out
 
 
@@ -307,6 +311,26 @@ class Mlp:
             pass
 
 
+def pcg_ragged(contexts, mus, xs, **kw):
+    """rb_pcg_ragged: RBCG on several contexts (one batch each, device x) in one launch
+    sequence; returns (status, [stats of each context])."""
+    n = len(contexts)
+    ctxs = (C.c_void_p * n)(*[c.handle for c in contexts])
+    mus = [_f64(m).reshape(-1, c.n_mu) for m, c in zip(mus, contexts)]
+    B = (C.c_int * n)(*[m.shape[0] for m in mus])
+    mu_p = (C.c_void_p * n)(*[_ptr(m) for m in mus])
+    x_p = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    sts = [(RbStats * max(m.shape[0], 1))() for m in mus]
+    st_p = (C.c_void_p * n)(*[C.cast(st, C.c_void_p) for st in sts])
+    o = make_opts(**kw)
+    status = lib().rb_pcg_ragged(C.cast(ctxs, C.c_void_p), n, C.cast(B, C.c_void_p), C.cast(mu_p, C.c_void_p),
+                                 C.cast(x_p, C.c_void_p), C.byref(o), C.cast(st_p, C.c_void_p))
+    if status not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN):
+        msgs = "; ".join(lib().rb_last_error(c.handle).decode() for c in contexts)
+        raise RbError(status, msgs or lib().rb_last_error(None).decode())
+    return status, [stats_array(st)[:m.shape[0]] for st, m in zip(sts, mus)]
+
+
 class Context:
     """An online RB context (rb_ctx*)."""
 
@@ -360,6 +384,10 @@ class Context:
         if st not in (RB_OK, RB_ENOCONV, RB_EBREAKDOWN):
             raise RbError(st, lib().rb_last_error(self._h).decode())
         return st
+
+    @property
+    def handle(self):
+        return self._h
 
     def save(self, path: str) -> None:
         self._check(lib().rb_save(self._h, path.encode()))
@@ -444,6 +472,10 @@ class Context:
             coef = np.zeros((B, self.n))
         self._check(lib().rb_coefficients(self._h, B, _ptr(x), _ptr(coef), C.c_void_p(int(stream) if stream else 0)))
         return coef
+
+    def debug_wait(self, limit_s: float = 2.0, skip_stage: int = -1) -> None:
+        """rb_debug_wait: limit of the kernels' bounded waits and the stage the test hook leaves out."""
+        self._check(lib().rb_debug_wait(self._h, limit_s, skip_stage))
 
     def profile(self, enable: bool) -> None:
         """rb_profile: time every kernel launch with CUDA events (graphs off) while enabled."""

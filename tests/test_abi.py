@@ -46,6 +46,7 @@ def test_binding_covers_the_header(libpath):
     lib = rb.lib()
     o = rb.make_opts()
     assert o.tol == 1e-10 and o.nu == 1 and o.beta_form == rb.BETAS["pr"]
+    assert o.adaptive_n == 0 and o.gamma == 10.0
     assert lib.rb_status_string(rb.RB_ENOCONV) == b"not converged"
 
 
@@ -53,7 +54,9 @@ def test_struct_layouts_match_header(libpath):
     """Field order / sizes of the ctypes mirrors agree with the C structs."""
     from paper_1804_06363_gb300 import rb
     assert ctypes.sizeof(rb.RbLoad) == 4 + 4 + 24 + 8
-    assert ctypes.sizeof(rb.RbStats) == 4 * 4 + 8
+    assert ctypes.sizeof(rb.RbStats) == 4 * 4 + 8 + 8       # n_used and the tail padding
+    assert rb.RbStats.n_used.offset == 24
+    assert rb.RbOpts.adaptive_n.offset == rb.RbOpts.store.offset + 4 and rb.RbOpts.gamma.offset % 8 == 0
     assert rb.RbOpts.stream.offset == ctypes.sizeof(rb.RbOpts) - 8
 
 
@@ -106,3 +109,34 @@ def test_network_parameter_layout_round_trip():
     for (W, b), (W2, b2) in zip(layers, back):
         np.testing.assert_array_equal(W, W2)
         np.testing.assert_array_equal(b, b2)
+
+
+def test_struct_layouts_match_compiled_header(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal what a C compiler makes of include/rb.h."""
+    import shutil
+    from paper_1804_06363_gb300 import rb
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {"rb_opts": (rb.RbOpts, ["tol", "nu", "omega", "inner_tol", "store", "adaptive_n", "gamma", "stream"]),
+              "rb_stats": (rb.RbStats, ["iters", "status", "rel_res", "n_used"]),
+              "rb_problem": (rb.RbProblem, ["dim", "m", "nb", "n_loads", "loads", "n_mu"]),
+              "rb_load": (rb.RbLoad, ["kind", "param", "center", "sigma"]),
+              "rb_tune_result": (rb.RbTuneResult, ["nu", "inner_tol", "ms_per_solve", "store"]),
+              "rb_kernel_time": (rb.RbKernelTime, ["name", "launches", "ms"])}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rb.h"', "int main(void) {"]
+    for cname, (_, fields) in checks.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for cname, (cls, fields) in checks.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f in fields:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)

@@ -57,3 +57,24 @@ def test_two_gloo_ranks_shard_and_agree_on_max():
     assert (a0, b0, a1, b1) == (0, 501, 501, 1001)
     assert t0 == t1 == 2.5
     assert c0 == c1 == 1001
+
+
+def test_bench_launches_its_own_ranks():
+    """bench.py --gpus 2 outside a launcher starts two ranks itself (torch.distributed.run on
+    127.0.0.1); --rank-check runs the rank logic on gloo without a GPU: the shards cover the
+    whole batch and every rank reports the maximum step time."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--rank-check",
+                        "--batch", "1000"], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["n_ranks"] == 2 and d["queries"] == 2000
+    shards = sorted(tuple(s) for s in d["shards"])
+    assert shards == [(0, 0, 1000), (1, 1000, 2000)]
+    assert d["t_max"] == 2.0
