@@ -83,6 +83,7 @@ def parse(argv=None):
     ap.add_argument("--warm-pairs", type=int, default=4096, help="training pairs (truth solves) of the network")
     ap.add_argument("--warm-steps", type=int, default=2000, help="Adam steps of the network")
     ap.add_argument("--warm-test", type=int, default=0, help="test queries of the comparison (default: the step's)")
+    ap.add_argument("--warm-modes", type=int, default=24, help="modes of the error basis of the warm start")
     ap.add_argument("--no-leg3d", action="store_true",
                     help="skip the 3D leg (128^3, 256 queries per step, timed after the 2D results)")
     ap.add_argument("--leg3d-steps", type=int, default=2)
@@ -286,8 +287,11 @@ T_START = time.perf_counter()
 
 
 def warm_start_experiment(ctx, w, args, opts, dev, stream):
-    """Learned warm start: a network trained on truth solves supplies x_0 = W c(mu); the
-    comparison times each start as a whole (starting vector + RBCG) on the same test queries."""
+    """Learned warm starts: networks trained on truth solves supply x_0 = W c(mu) (coefficients in
+    span(W)) or x_0 = x_hat(mu) + V z(mu) (an error basis V, the POD of x - x_hat over training
+    solutions, which leaves span(W)).  Each start is timed as a whole (starting vector + RBCG) on
+    the same test queries; the set-up (truth solves, POD, training) is reported beside it with the
+    number of solves after which it pays off."""
     import numpy as np
     import torch
 
@@ -297,52 +301,75 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
     N, n = prob.n_dof, ctx.n
     S = args.warm_pairs
     chunk = args.batch or w.batch
+    m_err = args.warm_modes
+    s_pod = min(256, chunk, S)
     mu_tr = wl.mlp_train_mu(w, S)
     Y = np.zeros((S, n))
+    Z = np.zeros((S, m_err))
     xb = torch.zeros((chunk, N), dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
+    pod_s = 0.0
     for c0 in range(0, S, chunk):
         m = np.ascontiguousarray(mu_tr[c0:c0 + chunk])
         ctx.pcg(m, xb[:len(m)], **opts)
         Y[c0:c0 + len(m)] = ctx.coefficients(xb[:len(m)], stream=stream.cuda_stream)
-    pairs_s = time.perf_counter() - t0
-    progress(f"warm start: {S} truth solves and their coefficients in {pairs_s:.1f} s")
+        if c0 == 0:
+            tp = time.perf_counter()
+            _, sig = ctx.error_basis(m[:s_pod], xb[:s_pod], m_err, stream=stream.cuda_stream)
+            pod_s = time.perf_counter() - tp
+        Z[c0:c0 + len(m)] = ctx.error_coefficients(m, xb[:len(m)], m_err, stream=stream.cuda_stream)
+    pairs_s = time.perf_counter() - t0 - pod_s
+    progress(f"warm start: {S} truth solves and their coefficients in {pairs_s:.1f} s, error basis "
+             f"({s_pod} snapshots, {m_err} modes) in {pod_s:.2f} s")
     del xb
     sizes = wl.mlp_layer_sizes(prob.n_mu, n)
+    sizes_e = wl.mlp_layer_sizes(prob.n_mu, m_err)
     net = rb.Mlp(prob.n_mu, prob.P, sizes[1], n, rb.flatten_params(wl.mlp_init(sizes)), max_samples=S)
+    net_e = rb.Mlp(prob.n_mu, prob.P, sizes_e[1], m_err, rb.flatten_params(wl.mlp_init(sizes_e)), max_samples=S)
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    hist = net.fit(mu_tr, Y, args.warm_steps, lr=3e-3, stream=stream.cuda_stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    train_ms = a.elapsed_time(b)
-    progress(f"warm start: {args.warm_steps} Adam steps in {train_ms:.0f} ms, loss {hist[0]:.3g} -> {hist[-1]:.3g}")
+    train = {}
+    for name, nt, targets in (("learned", net, Y), ("error_basis", net_e, Z)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hist = nt.fit(mu_tr, targets, args.warm_steps, lr=3e-3, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        train[name] = (a.elapsed_time(b), hist)
+        progress(f"warm start: {name} network, {args.warm_steps} Adam steps in {train[name][0]:.0f} ms, "
+                 f"loss {hist[0]:.3g} -> {hist[-1]:.3g}")
 
     T = args.warm_test or (args.batch or w.batch)
     mu = np.ascontiguousarray(w.draw_mu(w.test_seed, T))
     x = torch.zeros((T, N), dtype=torch.float64, device=dev)
     out = {"workload": w.name, "pairs": S, "pairs_solve_s": round(pairs_s, 2), "network": "x".join(map(str, sizes)),
-           "adam_steps": args.warm_steps, "train_ms": round(train_ms, 1),
-           "train_ms_per_step": round(train_ms / max(1, args.warm_steps), 4),
-           "loss_first_last": [float(hist[0]), float(hist[-1])] if len(hist) else None, "test_queries": T}
+           "error_basis": {"snapshots": s_pod, "modes": m_err, "pod_s": round(pod_s, 3),
+                           "singular_values_first_last": [float(sig[0]), float(sig[-1])],
+                           "network": "x".join(map(str, sizes_e))},
+           "adam_steps": args.warm_steps,
+           "train_ms": {k: round(v[0], 1) for k, v in train.items()},
+           "loss_first_last": {k: [float(v[1][0]), float(v[1][-1])] for k, v in train.items()},
+           "test_queries": T}
     ref = None
-    for name in ("cold", "galerkin", "learned"):
+
+    def start(name):
+        if name == "cold":
+            x.zero_()   # rb_pcg zeroes x itself for a cold start; this keeps x0 visible below
+        elif name == "galerkin":
+            ctx.warm_start(mu, x, stream=stream.cuda_stream)
+        elif name == "learned":
+            ctx.warm_start(mu, x, net=net, stream=stream.cuda_stream)
+        else:
+            ctx.warm_start_error(mu, x, net=net_e, stream=stream.cuda_stream)
+
+    for name in ("cold", "galerkin", "learned", "error_basis"):
         kw = {**opts, "x0": name != "cold"}
-        net_arg = net if name == "learned" else None
 
         def run():
-            if name == "cold":
-                x.zero_()   # rb_pcg zeroes x itself for a cold start; this keeps x0 visible below
-            else:
-                ctx.warm_start(mu, x, net=net_arg, stream=stream.cuda_stream)
+            start(name)
             return ctx.pcg(mu, x, **kw)
 
         run()                                    # warm-up
-        if name != "cold":
-            ctx.warm_start(mu, x, net=net_arg, stream=stream.cuda_stream)
-        else:
-            x.zero_()
+        start(name)
         x0 = x.clone()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -350,17 +377,27 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
         status, st = run()
         e1.record(stream)
         torch.cuda.synchronize()
-        s = e0.elapsed_time(e1) / 1000.0
+        s_ = e0.elapsed_time(e1) / 1000.0
         if ref is None:
             ref = x.clone()
         err0 = ((x0 - ref).norm(dim=1) / ref.norm(dim=1)).mean().item()
         dev_sol = ((x - ref).norm(dim=1) / ref.norm(dim=1)).max().item()
-        out[name] = {"solves_per_s": round(T / s, 1), "mean_iters": float(st["iters"].mean()),
+        out[name] = {"solves_per_s": round(T / s_, 1), "mean_iters": float(st["iters"].mean()),
                      "mean_outer": float(st["outer"].mean()), "all_converged": bool(np.all(st["status"] == 0)),
                      "max_rel_res": float(st["rel_res"].max()), "mean_initial_rel_error": err0,
                      "max_rel_diff_to_cold_solution": dev_sol}
         progress(f"warm start: {name}: {out[name]}")
+    # set-up cost of each learned start and the number of solves after which it pays off
+    v_cold = out["cold"]["solves_per_s"]
+    for name, extra in (("learned", train["learned"][0] / 1000.0),
+                        ("error_basis", train["error_basis"][0] / 1000.0 + pod_s)):
+        setup = pairs_s + extra
+        v = out[name]["solves_per_s"]
+        gain = 1.0 / v_cold - 1.0 / v
+        out[name]["setup_s"] = round(setup, 2)
+        out[name]["break_even_solves"] = round(setup / gain) if gain > 0 else None
     net.close()
+    net_e.close()
     return out
 
 

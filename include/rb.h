@@ -157,6 +157,18 @@ rb_status rb_offline_build(rb_ctx** out, const rb_problem* prob, int n_max, int 
                            const double* mu_train, const rb_build_opts* bopts,
                            const rb_opts* solve_opts, int max_batch);
 
+/* Multi-fidelity offline build (Section 4.2, last paragraph): the greedy of
+ * rb_offline_build runs on the coarse problem (the fine problem's block
+ * partition, loads and parameters on a coarser grid) and selects the
+ * parameter sample S_N; the snapshots of S_N are then solved on the fine grid
+ * (RBCG with W_{N-1}, as Alg. 4, in solve_opts->precision) and orthonormalised
+ * in the selection order into the fine basis.  A fine snapshot that falls inside
+ * the span of the previous ones is skipped.  RB_EINVAL when the two problems
+ * differ in anything but the grid. */
+rb_status rb_offline_build_mf(rb_ctx** out, const rb_problem* fine, const rb_problem* coarse, int n_max, int n_train,
+                              const double* mu_train, const rb_build_opts* bopts, const rb_opts* solve_opts,
+                              int max_batch);
+
 /* Basis file (.rbb): header, W, A_{N,q}, f_{N,r}, snapshot factor R,
  * selected training indices, FNV-1a checksum.  Load fails with RB_EFORMAT on a
  * bad magic, size or checksum and RB_EIO when the file cannot be read. */
@@ -281,6 +293,42 @@ rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* 
  */
 rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, double* x, double* coef,
                         void* stream);
+
+/*
+ * Error basis of the learned warm start.  A start in span(W) is sent by the
+ * first RB correction of Alg. 3 to about the same iterate (the paper's
+ * analysis of Alg. 2 from any start in span(W)), so the learned start that can
+ * gain leaves span(W): x_0 = x_hat(mu) + V z(mu), with x_hat = W a_N(mu) the RB
+ * approximation of eq. 3 and V an orthonormal basis of the errors
+ * e_s = x_s - x_hat(mu_s) of training solutions (the paper has no learned
+ * component; this is the benchmark spec's learned warm start).
+ *
+ * rb_error_basis: proper orthogonal decomposition of the errors of S training
+ * solutions by the method of snapshots (Gram matrix E^T E in FP64 on the
+ * device, its eigenpairs on the host): V = E Phi_m diag(lambda_m)^{-1/2}, m
+ * modes kept in the context (FP64 and an FP32 copy, allocated here; a later
+ * call replaces them).  mu host [S][n_mu] (diffusion coefficients > 0);
+ * X host or device [S][N_dof] (solutions, e.g. from rb_pcg); 1 <= S <=
+ * min(max_batch, 512); 1 <= m <= min(S, 64).  Z host or device [S][m] or
+ * NULL: Z = V^T E (the targets of a network); sigma host [m] or NULL: the
+ * singular values of E (a mode below 1e-12 of the largest is set to zero).
+ * Uses the context's workspace (not during a solve).
+ */
+rb_status rb_error_basis(rb_ctx* ctx, int S, const double* mu, const double* X, int m, double* Z, double* sigma,
+                         void* stream);
+
+/* Z_b = V^T (x_b - x_hat(mu_b)) for B solutions (host or device [B][N_dof]) and
+ * host mu [B][n_mu]; Z host or device [B][m].  FP32 products, FP64 sums.
+ * RB_EINVAL without an error basis. */
+rb_status rb_error_coefficients(rb_ctx* ctx, int B, const double* mu, const double* X, double* Z, void* stream);
+
+/* x_b = x_hat(mu_b) + V z_b with z_b from the network (net != NULL: n_in = n_mu,
+ * n_out = m) or given (z host or device [B][m], net == NULL; exactly one of the
+ * two).  x host or device [B][N_dof], written; the lifts run on FP32 copies of
+ * W and V (relative error about 1e-7; the solvers correct it).  A start for
+ * rb_pcg with rb_opts.x0_mode = RB_X0_GIVEN. */
+rb_status rb_warm_start_error(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, double* x, const double* z,
+                              void* stream);
 
 /* Reduced coefficients c_b = W^T x_b of given vectors (eq. 5 applied to x
  * instead of r): with an orthonormal W, W c_b is the orthogonal projection of

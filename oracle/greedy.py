@@ -1,4 +1,5 @@
-"""Greedy construction of the RB space: Alg. 1 and the adaptive variant Alg. 4.
+"""Greedy construction of the RB space: Alg. 1, the adaptive variant Alg. 4 and the
+multi-fidelity construction of Section 4.2 (last paragraph).
 
 Steps, per N = 1..N_max (Section 2.2):
   3. solve A(mu_N) x(mu_N) = f(mu_N) (sparse direct or CG for Alg. 1; RBCG with
@@ -71,21 +72,68 @@ def truth_solve(prob, mu, method: str, basis: rb.Basis | None, tol: float):
     raise ValueError(method)
 
 
+def grow(prob, basis: rb.Basis, x: np.ndarray, candidate: int, drop_tol: float = 1e-10):
+    """Steps 4-5 for one snapshot x: modified Gram-Schmidt (twice) against W, the new column of
+    W, the snapshot factor R and the new row and column of A_{N,q}, f_{N,r} (eq. 12c).
+    Returns the grown basis, or None when x lies inside span(W) (remainder below drop_tol ||x||)."""
+    Q, R = prob.P, len(prob.loads)
+    v, coeffs, nrm = mgs_twice(basis.W, x)
+    if nrm < drop_tol * np.linalg.norm(x):
+        return None
+    N = basis.N + 1
+    w = v / nrm
+    W = np.concatenate([basis.W, w[:, None]], axis=1)
+    Rf = np.zeros((N, N))
+    Rf[:N - 1, :N - 1] = basis.R
+    Rf[:N - 1, N - 1] = coeffs
+    Rf[N - 1, N - 1] = nrm
+    ANq = np.zeros((Q, N, N))
+    ANq[:, :N - 1, :N - 1] = basis.ANq
+    for q in range(Q):
+        col = W.T @ pb.affine_term(prob, q, w)
+        ANq[q, :, N - 1] = col
+        ANq[q, N - 1, :] = col
+    fNr = np.zeros((R, N))
+    fNr[:, :N - 1] = basis.fNr
+    for r in range(R):
+        fNr[r, N - 1] = w @ pb.load_term(prob, r)
+    return rb.Basis(prob, W, ANq, fNr, Rf, basis.selected + [candidate])
+
+
+def empty_basis(prob) -> rb.Basis:
+    return rb.Basis(prob, np.zeros((prob.n_dof, 0)), np.zeros((prob.P, 0, 0)), np.zeros((len(prob.loads), 0)),
+                    np.zeros((0, 0)), [])
+
+
+def multi_fidelity(prob, coarse, train_mu: np.ndarray, n_max: int, truth: str = "direct",
+                   score: str = "snapshot", truth_tol: float = 1e-13, drop_tol: float = 1e-10) -> rb.Basis:
+    """Section 4.2, last paragraph: the greedy runs on the coarse grid and selects the parameter
+    sample S_N; the snapshots of S_N are then solved on the fine grid (`prob`) and enter the fine
+    basis in the selection order (a snapshot inside the span of the earlier ones is skipped).
+    The coarse problem has the fine one's blocks, loads and parameters."""
+    sample = greedy(coarse, train_mu, n_max, truth, score, truth_tol, drop_tol).selected
+    basis = empty_basis(prob)
+    for j in sample:
+        x = truth_solve(prob, train_mu[j], truth, basis, truth_tol)
+        grown = grow(prob, basis, x, j, drop_tol)
+        if grown is not None:
+            basis = grown
+    return basis
+
+
 def greedy(prob, train_mu: np.ndarray, n_max: int, truth: str = "direct",
            score: str = "snapshot", truth_tol: float = 1e-13, drop_tol: float = 1e-10) -> rb.Basis:
     """Alg. 1 (truth = "direct" or "cg") or Alg. 4 (truth = "rbcg")."""
-    n_dof, Q, R = prob.n_dof, prob.P, len(prob.loads)
-    basis = rb.Basis(prob, np.zeros((n_dof, 0)), np.zeros((Q, 0, 0)), np.zeros((R, 0)),
-                     np.zeros((0, 0)), [])
+    basis = empty_basis(prob)
     excluded = set()
     candidate = 0                              # step 0: mu_1 = Xi_train[0]
     last_scores = None
     while basis.N < n_max:
         mu = train_mu[candidate]
         x = truth_solve(prob, mu, truth, basis, truth_tol)
-        v, coeffs, nrm = mgs_twice(basis.W, x)
+        grown = grow(prob, basis, x, candidate, drop_tol)
         excluded.add(candidate)
-        if nrm < drop_tol * np.linalg.norm(x):
+        if grown is None:
             if last_scores is None:
                 raise RuntimeError("first snapshot is zero")
             s = last_scores.copy()
@@ -94,25 +142,7 @@ def greedy(prob, train_mu: np.ndarray, n_max: int, truth: str = "direct",
                 break
             candidate = int(np.argmax(s))
             continue
-        N = basis.N + 1
-        w = v / nrm
-        W = np.concatenate([basis.W, w[:, None]], axis=1)
-        Rf = np.zeros((N, N))
-        Rf[:N - 1, :N - 1] = basis.R
-        Rf[:N - 1, N - 1] = coeffs
-        Rf[N - 1, N - 1] = nrm
-        # eq. 12c, new row and column only
-        ANq = np.zeros((Q, N, N))
-        ANq[:, :N - 1, :N - 1] = basis.ANq
-        for q in range(Q):
-            col = W.T @ pb.affine_term(prob, q, w)
-            ANq[q, :, N - 1] = col
-            ANq[q, N - 1, :] = col
-        fNr = np.zeros((R, N))
-        fNr[:, :N - 1] = basis.fNr
-        for r in range(R):
-            fNr[r, N - 1] = w @ pb.load_term(prob, r)
-        basis = rb.Basis(prob, W, ANq, fNr, Rf, basis.selected + [candidate])
+        basis = grown
         if basis.N == n_max:
             break
         last_scores = scores(basis, train_mu, score)

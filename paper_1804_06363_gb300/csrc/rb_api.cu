@@ -119,6 +119,10 @@ struct rb_ctx {
     bool force_generic = false;       // testing: use the generic stencil kernels everywhere
     unsigned long long wait_ns = 2000000000ull;   // limit of the kernels' bounded waits (rb_debug_wait)
     long long dbg_skip = -1;                      // test hook of rb_debug_wait
+    // error basis of the learned warm start (rb_error_basis): V [m_err][N], FP64 and FP32
+    int m_err = 0;
+    double* d_V64 = nullptr;
+    float* d_V32 = nullptr;
     // the captured graph of the last solve (reused while its launch parameters stay the same)
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<unsigned char> graph_key;
@@ -344,6 +348,8 @@ void ctx_destroy(rb_ctx* ctx) {
     cudaDeviceSynchronize();
     tc_free(ctx->tc);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->d_V64) cudaFree(ctx->d_V64);
+    if (ctx->d_V32) cudaFree(ctx->d_V32);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
@@ -1398,6 +1404,186 @@ rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, doubl
     CK(cudaMemcpyAsync(&notspd, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (notspd) { ctx->err = "A_N(mu) is not positive definite for some query"; return RB_EBREAKDOWN; }
+    return RB_OK;
+}
+
+namespace {
+
+// Galerkin coefficients a_N(mu_b) of eq. 2 for B <= Bmax host parameter vectors into coef
+// (device [B][n]); RB_EBREAKDOWN when some A_N(mu_b) is not SPD
+rb_status galerkin_device(rb_ctx* ctx, int B, const double* mu, double* coef, cudaStream_t s) {
+    LoadMap lm{};
+    for (int r = 0; r < ctx->R; ++r) lm.param[r] = ctx->load_param[r];
+    CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    CK(cudaMemcpyAsync(ctx->d_mu, mu, (size_t)B * ctx->n_mu * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_galerkin(ctx->n, ctx->P, ctx->d_ANq, ctx->R, lm, ctx->d_fNr, ctx->n_mu, B, ctx->d_mu, coef, ctx->d_flag, s);
+    CK(cudaGetLastError());
+    int notspd = 0;
+    CK(cudaMemcpyAsync(&notspd, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (notspd) { ctx->err = "A_N(mu) is not positive definite for some query"; return RB_EBREAKDOWN; }
+    return RB_OK;
+}
+
+rb_status check_mu_positive(rb_ctx* ctx, int B, const double* mu) {
+    if (pointer_kind(mu) != PTR_HOST) { ctx->err = "mu must be host memory"; return RB_EINVAL; }
+    for (size_t i = 0; i < (size_t)B * ctx->n_mu; ++i)
+        if (!std::isfinite(mu[i]) || ((int)(i % ctx->n_mu) < ctx->P && !(mu[i] > 0.0))) {
+            ctx->err = "parameter vectors must be finite, with positive diffusion coefficients";
+            return RB_EINVAL;
+        }
+    return RB_OK;
+}
+
+// E = X - W a_N(mu) for B <= Bmax solutions X (host or device) into ctx->d_r64
+rb_status errors_device(rb_ctx* ctx, int B, const double* mu, const double* X, cudaStream_t s) {
+    const long long N = ctx->N;
+    bool bad = false;
+    const bool dx = is_device_ptr(ctx, X, &bad);
+    if (bad) return RB_EINVAL;
+    const double* Xd = X;
+    if (!dx) {
+        CK(cudaMemcpyAsync(ctx->d_x64, X, (size_t)B * N * sizeof(double), cudaMemcpyHostToDevice, s));
+        Xd = ctx->d_x64;
+    }
+    double* a = ctx->d_scratch;   // [B][n]
+    TRY(galerkin_device(ctx, B, mu, a, s));
+    launch_eb_errors(N, ctx->n, ctx->d_W64c, B, a, Xd, ctx->d_r64, ctx->grid, s);
+    CK(cudaGetLastError());
+    return RB_OK;
+}
+
+}  // namespace
+
+rb_status rb_error_basis(rb_ctx* ctx, int S, const double* mu, const double* X, int m, double* Z, double* sigma,
+                         void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (S < 1 || S > ctx->Bmax || S > 512 || m < 1 || m > 64 || m > S || !mu || !X || ctx->n == 0) {
+        ctx->err = "need 1 <= m <= min(S, 64), 1 <= S <= min(max_batch, 512), mu, X and a basis";
+        return RB_EINVAL;
+    }
+    TRY(check_mu_positive(ctx, S, mu));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    if ((size_t)2 * ctx->Bmax * N < eb_gram_part_elems(S) || ctx->scratch_bytes / sizeof(double) < (size_t)S * S) {
+        ctx->err = "grid too small for the Gram partial sums of this many snapshots";
+        return RB_EINVAL;
+    }
+    TRY(errors_device(ctx, S, mu, X, s));
+    // Gram matrix E^T E: partial sums in the (idle) FP64 direction workspace, the sum in scratch
+    double* G = ctx->d_scratch;
+    launch_eb_gram(N, S, ctx->d_r64, ctx->d_p64, G, ctx->grid, s);
+    CK(cudaGetLastError());
+    std::vector<double> Gh((size_t)S * S), lam, Phi;
+    CK(cudaMemcpyAsync(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    jacobi_eigen(S, Gh, lam, Phi);
+    // modes whose singular value is below 1e-12 of the largest carry nothing: zero columns
+    std::vector<double> C((size_t)S * m, 0.0), sig(m, 0.0);
+    for (int k = 0; k < m; ++k) {
+        const double l = lam[k] > 0.0 ? lam[k] : 0.0;
+        sig[k] = std::sqrt(l);
+        if (!(sig[k] > 1e-12 * std::sqrt(std::max(lam[0], 0.0)))) { sig[k] = 0.0; continue; }
+        for (int i = 0; i < S; ++i) C[(size_t)i * m + k] = Phi[(size_t)i * S + k] / sig[k];
+    }
+    if (ctx->m_err != m) {
+        if (ctx->d_V64) cudaFree(ctx->d_V64);
+        if (ctx->d_V32) cudaFree(ctx->d_V32);
+        ctx->d_V64 = nullptr;
+        ctx->d_V32 = nullptr;
+        ctx->m_err = 0;
+        if (cudaMalloc((void**)&ctx->d_V64, (size_t)m * N * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&ctx->d_V32, (size_t)m * N * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->err = "allocation of the error basis failed";
+            return RB_ENOMEM;
+        }
+    }
+    double* dC = ctx->d_scratch;   // G is no longer needed
+    CK(cudaMemcpyAsync(dC, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_eb_modes(N, S, m, ctx->d_r64, dC, ctx->d_V64, ctx->d_V32, ctx->grid, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    ctx->m_err = m;
+    // Z = V^T E = diag(sigma) Phi_m^T, [S][m]
+    if (Z) {
+        std::vector<double> Zh((size_t)S * m);
+        for (int i = 0; i < S; ++i)
+            for (int k = 0; k < m; ++k) Zh[(size_t)i * m + k] = sig[k] * Phi[(size_t)i * S + k];
+        CK(cudaMemcpyAsync(Z, Zh.data(), Zh.size() * sizeof(double), cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (sigma) std::copy(sig.begin(), sig.end(), sigma);
+    return RB_OK;
+}
+
+rb_status rb_error_coefficients(rb_ctx* ctx, int B, const double* mu, const double* X, double* Z, void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!mu || !X || !Z))) { ctx->err = "B < 0 or NULL mu / X / Z"; return RB_EINVAL; }
+    if (ctx->m_err == 0) { ctx->err = "the context has no error basis (rb_error_basis)"; return RB_EINVAL; }
+    TRY(check_mu_positive(ctx, B, mu));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const int m = ctx->m_err;
+    bool bad = false;
+    const bool dX = is_device_ptr(ctx, X, &bad), dZ = is_device_ptr(ctx, Z, &bad);
+    if (bad) return RB_EINVAL;
+    const size_t sd = ctx->scratch_bytes / sizeof(double);
+    int chunk = std::min(ctx->Bmax, 256);
+    while (chunk > 1 && (size_t)coef_splits(chunk, ctx->num_sms) * chunk * m + (size_t)chunk * (ctx->n + m) > sd)
+        chunk /= 2;
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int nbw = std::min(chunk, B - b0);
+        TRY(errors_device(ctx, nbw, mu + (size_t)b0 * ctx->n_mu, dX ? X + (size_t)b0 * N : X + (size_t)b0 * N, s));
+        double* zc = dZ ? Z + (size_t)b0 * m : ctx->d_scratch + (size_t)chunk * ctx->n;
+        launch_coefficients(N, m, ctx->d_V32, nbw, ctx->d_r64, zc, ctx->d_scratch + (size_t)chunk * (ctx->n + m),
+                            ctx->num_sms, s);
+        CK(cudaGetLastError());
+        if (!dZ) CK(cudaMemcpyAsync(Z + (size_t)b0 * m, zc, (size_t)nbw * m * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RB_OK;
+}
+
+rb_status rb_warm_start_error(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, double* x, const double* z,
+                              void* stream) {
+    if (!ctx) return RB_EINVAL;
+    if (B < 0 || (B > 0 && (!mu || !x))) { ctx->err = "B < 0 or NULL mu / x"; return RB_EINVAL; }
+    if (ctx->m_err == 0) { ctx->err = "the context has no error basis (rb_error_basis)"; return RB_EINVAL; }
+    if ((net == nullptr) == (z == nullptr)) { ctx->err = "give exactly one of a network and coefficients z"; return RB_EINVAL; }
+    if (net && (mlp_n_in(net) != ctx->n_mu || mlp_n_out(net) != ctx->m_err)) {
+        ctx->err = "the network must map n_mu parameters to the m coefficients of the error basis";
+        return RB_EINVAL;
+    }
+    if (net && !mlp_ready(net)) { ctx->err = "the network has not been fitted"; return RB_EINVAL; }
+    TRY(check_mu_positive(ctx, B, mu));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+    const long long N = ctx->N;
+    const int n = ctx->n, m = ctx->m_err;
+    bool bad = false;
+    const bool dx = is_device_ptr(ctx, x, &bad);
+    const bool dz = z && is_device_ptr(ctx, z, &bad);
+    if (bad) return RB_EINVAL;
+    const int chunk = std::max(1, std::min<int>(ctx->Bmax, (int)(ctx->scratch_bytes / sizeof(double)) / (n + m)));
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int nbw = std::min(chunk, B - b0);
+        double* a = ctx->d_scratch;
+        double* zc = ctx->d_scratch + (size_t)chunk * n;
+        TRY(galerkin_device(ctx, nbw, mu + (size_t)b0 * ctx->n_mu, a, s));
+        if (net) {
+            rb_status st = mlp_predict_device(net, nbw, ctx->d_mu, ctx->n_mu, zc, s);
+            if (st != RB_OK) { ctx->err = "network evaluation failed"; return st; }
+        } else {
+            CK(cudaMemcpyAsync(zc, z + (size_t)b0 * m, (size_t)nbw * m * sizeof(double),
+                               dz ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        }
+        double* xs = dx ? x + (size_t)b0 * N : ctx->d_x64;
+        launch_lift(N, n, ctx->d_W32c, nbw, a, xs, ctx->grid, s);
+        launch_eb_lift_add(N, m, ctx->d_V32, nbw, zc, xs, ctx->grid, s);
+        CK(cudaGetLastError());
+        if (!dx) CK(cudaMemcpyAsync(x + (size_t)b0 * N, xs, (size_t)nbw * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
     return RB_OK;
 }
 

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rb.h"
 
@@ -398,6 +399,17 @@ void launch_lift(long long n, int nb, const float* W32c, int B, const double* co
 int coef_splits(int B, int num_sms);
 void launch_coefficients(long long n, int nb, const float* W32c, int B, const double* X, double* coef,
                          double* scratch, int num_sms, cudaStream_t s);            // c_b = W^T x_b
+
+// error basis of the learned warm start (rb_errbasis.cu)
+void launch_eb_errors(long long n, int nb, const double* W64c, int S, const double* a, const double* X, double* E,
+                      int grid, cudaStream_t s);                                   // E = X - W a
+size_t eb_gram_part_elems(int S);
+void launch_eb_gram(long long n, int S, const double* E, double* part, double* G, int grid, cudaStream_t s);
+void launch_eb_modes(long long n, int S, int m, const double* E, const double* C, double* V64, float* V32, int grid,
+                     cudaStream_t s);                                              // V = E C
+void launch_eb_lift_add(long long n, int m, const float* V32, int B, const double* z, double* x, int grid,
+                        cudaStream_t s);                                           // x_b += V z_b
+void jacobi_eigen(int S, std::vector<double>& A, std::vector<double>& lam, std::vector<double>& Phi);
 
 // learned warm start (rb_mlp.cu)
 int mlp_n_in(const rb_mlp* net);

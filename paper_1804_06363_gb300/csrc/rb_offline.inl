@@ -29,8 +29,11 @@ struct BuildBufs {
     double* Rsnap = nullptr;    // [MAX_N][MAX_N]
 };
 
+// order == nullptr: Alg. 1 (the next parameter is the argmax of the scores).  Otherwise the
+// parameters are taken in the given order (the sample selected on a coarse grid) and no scores
+// are computed.
 rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_train, const rb_build_opts& b,
-                       const rb_opts& so) {
+                       const rb_opts& so, const std::vector<int>* order = nullptr) {
     const long long N = ctx->N;
     const int Q = ctx->P, R = ctx->R, n_mu = ctx->n_mu;
     BuildBufs bb;
@@ -72,7 +75,9 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
     ctx->selected.clear();
     std::vector<char> excluded(n_train, 0);
     std::vector<double> last_scores;
-    int cand = 0;
+    size_t next_in_order = 0;
+    if (order && order->empty()) { ctx->err = "empty parameter sample"; return RB_EINVAL; }
+    int cand = order ? (*order)[next_in_order++] : 0;
     std::vector<double> c1(MAX_N), c2(MAX_N);
     while (ctx->n < n_max) {
         const int n = ctx->n;
@@ -104,7 +109,13 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
         }
         const double nrm = launch_norm(ctx->geo, bb.snap, ctx->d_scratch, s);
         if (!(nrm >= b.drop_tol * xnorm) || !(nrm > 0.0)) {
-            // numerically inside span W: take the next best candidate of the last scores
+            // numerically inside span W: take the next candidate of the sample, or the next best
+            // candidate of the last scores
+            if (order) {
+                if (next_in_order >= order->size()) break;
+                cand = (*order)[next_in_order++];
+                continue;
+            }
             if (last_scores.empty()) { ctx->err = "first snapshot is zero"; return RB_EBREAKDOWN; }
             int best = -1;
             for (int t = 0; t < n_train; ++t)
@@ -153,6 +164,11 @@ rb_status build_greedy(rb_ctx* ctx, int n_max, int n_train, const double* mu_tra
         ctx->n = n1;
         TRY(ctx_refresh_basis(ctx));
         if (ctx->n == n_max) break;
+        if (order) {
+            if (next_in_order >= order->size()) break;
+            cand = (*order)[next_in_order++];
+            continue;
+        }
         // steps 5-6: score every training parameter
         CK(cudaMemcpy(bb.Rsnap, ctx->h_Rsnap.data(), (size_t)n1 * n1 * sizeof(double), cudaMemcpyHostToDevice));
         launch_scores(ctx->geo, Q, R, bb.lparam, n_mu, n1, ctx->nbp, ctx->d_ANq, ctx->d_fNr, bb.Rsnap, n_train,
@@ -226,6 +242,53 @@ rb_status rb_offline_build(rb_ctx** out, const rb_problem* prob, int n_max, int 
     rb_status s = ctx_init(ctx, prob, n_max, max_batch);
     if (s == RB_OK) s = validate_opts(ctx, so);
     if (s == RB_OK) s = build_greedy(ctx, n_max, n_train, mu_train, b, so);
+    if (s != RB_OK) {
+        g_create_error = ctx->err;
+        ctx_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return RB_OK;
+}
+
+rb_status rb_offline_build_mf(rb_ctx** out, const rb_problem* fine, const rb_problem* coarse, int n_max, int n_train,
+                              const double* mu_train, const rb_build_opts* bopts, const rb_opts* solve_opts,
+                              int max_batch) {
+    if (!out) { g_create_error = "out is NULL"; return RB_EINVAL; }
+    *out = nullptr;
+    std::string why;
+    if (validate_problem(fine, why) != RB_OK || validate_problem(coarse, why) != RB_OK) {
+        g_create_error = why;
+        return RB_EINVAL;
+    }
+    bool same = fine->dim == coarse->dim && fine->n_loads == coarse->n_loads && fine->n_mu == coarse->n_mu;
+    for (int d = 0; d < 3 && same; ++d) same = fine->nb[d] == coarse->nb[d];
+    for (int r = 0; r < fine->n_loads && same; ++r) {
+        const rb_load &a = fine->loads[r], &c = coarse->loads[r];
+        same = a.kind == c.kind && a.param == c.param && a.sigma == c.sigma && a.center[0] == c.center[0] &&
+               a.center[1] == c.center[1] && a.center[2] == c.center[2];
+    }
+    if (!same) {
+        g_create_error = "the coarse problem must have the fine one's blocks, loads and parameters";
+        return RB_EINVAL;
+    }
+    // the parameter sample S_N: the greedy on the coarse grid
+    rb_ctx* cctx = nullptr;
+    rb_status s = rb_offline_build(&cctx, coarse, n_max, n_train, mu_train, bopts, solve_opts, 1);
+    if (s != RB_OK) return s;
+    const std::vector<int> order = cctx->selected;
+    ctx_destroy(cctx);
+    // the fine snapshots of S_N, in the selection order
+    rb_build_opts b;
+    rb_default_build_opts(&b);
+    if (bopts) b = *bopts;
+    rb_opts so;
+    rb_default_opts(&so);
+    if (solve_opts) so = *solve_opts;
+    rb_ctx* ctx = new rb_ctx();
+    s = ctx_init(ctx, fine, (int)order.size(), max_batch);
+    if (s == RB_OK) s = validate_opts(ctx, so);
+    if (s == RB_OK) s = build_greedy(ctx, (int)order.size(), n_train, mu_train, b, so, &order);
     if (s != RB_OK) {
         g_create_error = ctx->err;
         ctx_destroy(ctx);

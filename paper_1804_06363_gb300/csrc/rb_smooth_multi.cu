@@ -208,20 +208,23 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
         unsigned cslot = seq % RING_N, cpar = (seq / RING_N) & 1u;
 
         // one step of the march; PAR = k & 1: every half-sweep updates columns PAR, PAR + 2
-        auto step = [&](auto par_tag, int k) {
+        // UNI: the rows k .. k-NH+1 share one key (uniform across the CTA), so every half-sweep
+        // uses cf; otherwise each forms its own coefficients
+        auto step = [&](auto par_tag, auto uni_tag, int k) {
             constexpr int PAR = decltype(par_tag)::value;
+            constexpr bool UNI = decltype(uni_tag)::value != 0;
             constexpr int J0 = PAR, J1 = PAR + 2;          // updated columns
             constexpr int K0 = 1 - PAR, K1 = 3 - PAR;      // the other colour's columns
             if (ok && !mb_wait(full + cslot, cpar, P.err, P.wait_ns)) ok = false;
             const uint32_t o_cur = cslot * stage_b;
             const uint32_t o_prev = ((cslot + RING_N - 1) % RING_N) * stage_b;
-            // coefficients: one set while rows k .. k-NH+1 share a key
-            const int kt = min(max(k, 0), my - 1), kb = min(max(k - NH + 1, 0), my - 1);
-            const int key_t = __ldg(g.rkey + kt), key_b = __ldg(g.rkey + kb);
-            const bool uniform = key_t == key_b;
-            if (uniform && key_t != ckey) {
-                tcoef<float>(g, mus, x0, kt, cf);
-                ckey = key_t;
+            if constexpr (UNI) {
+                const int kt = min(max(k, 0), my - 1);
+                const int key_t = __ldg(g.rkey + kt);
+                if (key_t != ckey) {
+                    tcoef<float>(g, mus, x0, kt, cf);
+                    ckey = key_t;
+                }
             }
             // ---- H_0: red half-sweep of row k from the old source values
             {
@@ -238,9 +241,14 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
                 hc[0][1] = hp[0][1];
                 float n0 = 0.f, n1 = 0.f;
                 if (k >= y0 - NH + 1 && k >= 0 && k < my) {
-                    TCoef<float> own;
-                    if (!uniform) tcoef<float>(g, mus, x0, k, own);
-                    const MsCoef c = ms_pick<J0>(uniform ? cf : own);
+                    MsCoef c;
+                    if constexpr (UNI) {
+                        c = ms_pick<J0>(cf);
+                    } else {
+                        TCoef<float> own;
+                        tcoef<float>(g, mus, x0, k, own);
+                        c = ms_pick<J0>(own);
+                    }
                     const V4t<float> rk = ld4(o_cur + rx0);
                     // source row k (previous stage) across the thread edge
                     const float halo = PAR == 0 ? ld1(o_prev + sx0 - 4) : ld1(o_prev + sx0 + 16);
@@ -266,9 +274,14 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
                 hc[h][1] = hp[h][1];
                 float n0 = 0.f, n1 = 0.f;
                 if (r >= y0 - (NH - 1 - h) && r >= 0 && r < my) {
-                    TCoef<float> own;
-                    if (!uniform) tcoef<float>(g, mus, x0, r, own);
-                    const MsCoef c = ms_pick<J0>(uniform ? cf : own);
+                    MsCoef c;
+                    if constexpr (UNI) {
+                        c = ms_pick<J0>(cf);
+                    } else {
+                        TCoef<float> own;
+                        tcoef<float>(g, mus, x0, r, own);
+                        c = ms_pick<J0>(own);
+                    }
                     const uint32_t o_r = ((cslot + RING_N - (unsigned)h) % RING_N) * stage_b;   // stage of row r
                     const V4t<float> rb = ld4(o_r + rx0);
                     // H_{i-1}'s value across the thread edge of row r (written in the previous step)
@@ -306,8 +319,8 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
                             const V4t<float> pm = ld4(o_m + px0), pc = ld4(o_r + px0), pn = ld4(o_p + px0);
                             const float pl = ld1(o_r + px0 - 4), pr = ld1(o_r + px0 + 16);
                             TCoef<float> own;
-                            if (!uniform) tcoef<float>(g, mus, x0, r, own);
-                            const TCoef<float>& c = uniform ? cf : own;
+                            if constexpr (!UNI) tcoef<float>(g, mus, x0, r, own);
+                            const TCoef<float>& c = UNI ? cf : own;
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const float xl = j == 0 ? pl : pc.v[j - 1];
@@ -334,8 +347,17 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
             }
         };
         for (int k = kfirst; k <= klast; k += 2) {
-            step(Par1{}, k);
-            if (k + 1 <= klast) step(Par0{}, k + 1);
+            // rows k .. k-NH+1 (clamped to the grid) share a key: uniform over the CTA
+            auto uniform = [&](int kk) {
+                const int kt = min(max(kk, 0), my - 1), kb = min(max(kk - NH + 1, 0), my - 1);
+                return __ldg(g.rkey + kt) == __ldg(g.rkey + kb);
+            };
+            if (uniform(k)) step(Par1{}, Par1{}, k);
+            else step(Par1{}, Par0{}, k);
+            if (k + 1 <= klast) {
+                if (uniform(k + 1)) step(Par0{}, Par1{}, k + 1);
+                else step(Par0{}, Par0{}, k + 1);
+            }
         }
         if (LAST) {
             double v[2];

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
     long long pw = blockIdx.x;
     int pz = 0, pz1 = 0, pz0 = 0, py0 = 0, pqa = 0, pqb = 0;
     bool puse_old = false;
-    unsigned issued = 0;
+    unsigned issued = 0, pslot = 0;   // stages issued, slot of the next one
     auto cursor_item = [&](long long w) {
         for (; w < total; w += gridDim.x) {
             const int slot = (int)(w / per_q), rem = (int)(w % per_q);
@@ -327,8 +327,10 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
     auto issue_next = [&]() {
         if (pw >= total) return;
         const unsigned u = issued++;
-        T* st = ring + (size_t)(u % (unsigned)z.ring) * z.stage_elems;
-        uint64_t* b = bar + u % (unsigned)z.ring;
+        (void)u;
+        T* st = ring + (size_t)pslot * z.stage_elems;
+        uint64_t* b = bar + pslot;
+        if (++pslot == (unsigned)z.ring) pslot = 0;
         const int pl = pz + 1;   // plane of the stencil operand (out of the grid: zeros)
         if (PART_A) {
             mb_arrive_tx(b, tbytes_a + (puse_old ? tbytes_b : 0u));
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
         for (int i = 0; i < z.ring; ++i) issue_next();
     }
 
-    unsigned seq = 0;
+    unsigned seq = 0, cs = 0, cph = 0;   // steps so far, slot and phase parity of the current stage
     bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / per_q), rem = (int)(w % per_q);
@@ -376,11 +378,10 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
         T acc = T(0);
         const uint32_t own = (uint32_t)((tr + 1) * mx + x0);   // row y of the a (and b) box (rows from y0-1)
         for (int k = z0 - 2; k <= z1 - 1; ++k) {
-            const unsigned cs = seq % (unsigned)z.ring;
             if (!producer) {
                 const T* sg = ring + (size_t)cs * z.stage_elems;
-                const T* sp = ring + (size_t)((seq + z.ring - 1) % (unsigned)z.ring) * z.stage_elems;   // stage k-1
-                if (ok && !mb_wait(bar + cs, (seq / (unsigned)z.ring) & 1u, P.err, P.wait_ns)) ok = false;
+                const T* sp = ring + (size_t)(cs == 0 ? z.ring - 1 : cs - 1) * z.stage_elems;   // stage k-1
+                if (ok && !mb_wait(bar + cs, cph, P.err, P.wait_ns)) ok = false;
                 if (col_ok) {
                     V4t<T> a = lds4(sg + z.off_a + own);
                     if (use_old) {
@@ -440,6 +441,10 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
             // stage seq-1 had its last read in this step: refill its slot
             if (issuer && seq >= 1) issue_next();
             ++seq;
+            if (++cs == (unsigned)z.ring) {
+                cs = 0;
+                cph ^= 1u;
+            }
         }
         if (__syncthreads_or(!ok)) {
             if (issuer) zdrain(bar, issued, (unsigned)z.ring, P.wait_ns);
@@ -497,7 +502,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P,
     long long pw = blockIdx.x;
     int pz = 0, pz1 = 0, pz0 = 0, py0 = 0, pq = 0, pqp = 0;
     bool pap = false;
-    unsigned issued = 0;
+    unsigned issued = 0, pslot = 0;   // stages issued, slot of the next one
     auto cursor_item = [&](long long w) {
         for (; w < total; w += gridDim.x) {
             const int slot = (int)(w / per_q), rem = (int)(w % per_q);
@@ -518,8 +523,10 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P,
     auto issue_next = [&]() {
         if (pw >= total) return;
         const unsigned u = issued++;
-        T* st = ring + (size_t)(u % (unsigned)z.ring) * z.stage_elems;
-        uint64_t* b = bar + u % (unsigned)z.ring;
+        (void)u;
+        T* st = ring + (size_t)pslot * z.stage_elems;
+        uint64_t* b = bar + pslot;
+        if (++pslot == (unsigned)z.ring) pslot = 0;
         const bool rb = pz >= pz0 - 2;   // b (and p) of plane pz+1 are read from here on
         const bool rp = rb && pap;
         mb_arrive_tx(b, tbytes_a + (rb ? tbytes_b : 0u) + (rp ? tbytes_c : 0u));
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P,
         for (int i = 0; i < z.ring; ++i) issue_next();
     }
 
-    unsigned seq = 0;
+    unsigned seq = 0, cs = 0, cph = 0;   // steps so far, slot and phase parity of the current stage
     bool ok = true;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         const int slot = (int)(w / per_q), rem = (int)(w % per_q);
@@ -569,10 +576,9 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P,
             constexpr int PZ = decltype(pz_tag)::value, RP = decltype(rp_tag)::value;
             constexpr int J0 = (RP + PZ + 1) & 1, J1 = J0 + 2;   // updated columns of this step
             constexpr int K0 = 1 - J0, K1 = K0 + 2;              // the other two
-            const unsigned cs = seq % (unsigned)z.ring;
             const T* sg = ring + (size_t)cs * z.stage_elems;
-            const T* sp = ring + (size_t)((seq + z.ring - 1) % (unsigned)z.ring) * z.stage_elems;   // stage k-1
-            if (ok && !mb_wait(bar + cs, (seq / (unsigned)z.ring) & 1u, P.err, P.wait_ns)) ok = false;
+            const T* sp = ring + (size_t)(cs == 0 ? z.ring - 1 : cs - 1) * z.stage_elems;   // stage k-1
+            if (ok && !mb_wait(bar + cs, cph, P.err, P.wait_ns)) ok = false;
             if (col_ok) {
                 // source plane k+2 at the columns J (black there)
                 const V4t<T> s2 = lds4(sg + z.off_a + own_s);
@@ -667,6 +673,10 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P,
             __syncthreads();
             if (issuer && seq >= 1) issue_next();
             ++seq;
+            if (++cs == (unsigned)z.ring) {
+                cs = 0;
+                cph ^= 1u;
+            }
         };
         // steps k = z0-4 .. z1-1 (z0 even): the first two only load the source planes z0-2, z0-1
         for (int k = z0 - 4; k <= z1 - 1; k += 2) {

@@ -71,6 +71,8 @@ SIGNATURES = {
                                          C.c_void_p, C.c_void_p, C.c_int]),
     "rb_offline_build": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(RbProblem), C.c_int, C.c_int, C.c_void_p,
                                    C.POINTER(RbBuildOpts), C.POINTER(RbOpts), C.c_int]),
+    "rb_offline_build_mf": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(RbProblem), C.POINTER(RbProblem), C.c_int,
+                                      C.c_int, C.c_void_p, C.POINTER(RbBuildOpts), C.POINTER(RbOpts), C.c_int]),
     "rb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "rb_offline_load": (C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_int]),
     "rb_debug_wait": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong]),
@@ -91,6 +93,11 @@ SIGNATURES = {
     "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
     "rb_warm_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_error_basis": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "rb_error_coefficients": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rb_warm_start_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "rb_coefficients": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rb_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "rb_mlp_num_params": (C.c_int, [C.c_void_p]),
@@ -374,6 +381,22 @@ class Context:
         return cls._check_create(st, h)
 
     @classmethod
+    def build_multi_fidelity(cls, prob, coarse, n_max: int, train_mu, max_batch: int = 1, truth_tol: float = 1e-11,
+                             **solve_kw) -> "Context":
+        """rb_offline_build_mf: parameter sample by the greedy on the coarse problem, snapshots on prob."""
+        p, keep = make_problem(prob)
+        pc, keepc = make_problem(coarse)
+        mu = _f64(train_mu)
+        b = RbBuildOpts()
+        lib().rb_default_build_opts(C.byref(b))
+        b.truth_tol = truth_tol
+        o = make_opts(**solve_kw)
+        h = C.c_void_p()
+        st = lib().rb_offline_build_mf(C.byref(h), C.byref(p), C.byref(pc), n_max, mu.shape[0], _ptr(mu), C.byref(b),
+                                       C.byref(o), max_batch)
+        return cls._check_create(st, h)
+
+    @classmethod
     def load(cls, path: str, max_batch: int = 1) -> "Context":
         h = C.c_void_p()
         st = lib().rb_offline_load(C.byref(h), path.encode(), max_batch)
@@ -464,6 +487,34 @@ class Context:
         return self._check(lib().rb_warm_start(self._h, net.handle if net is not None else None, mu.shape[0],
                                                _ptr(mu), _ptr(x), _ptr(coef),
                                                C.c_void_p(int(stream) if stream else 0)))
+
+    def error_basis(self, mu, X, m: int, stream: Optional[int] = None):
+        """rb_error_basis: POD of the errors x_s - x_hat(mu_s) of S solutions X [S][N_dof] (host or
+        device); returns (Z = V^T E [S][m], singular values [m]) and keeps V in the context."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        S = mu.shape[0]
+        Z = np.zeros((S, m))
+        sig = np.zeros(m)
+        self._check(lib().rb_error_basis(self._h, S, _ptr(mu), _ptr(X), m, _ptr(Z), _ptr(sig),
+                                         C.c_void_p(int(stream) if stream else 0)))
+        return Z, sig
+
+    def error_coefficients(self, mu, X, m: int, Z=None, stream: Optional[int] = None):
+        """rb_error_coefficients: V^T (x_b - x_hat(mu_b)) for solutions X [B][N_dof]."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        if Z is None:
+            Z = np.zeros((mu.shape[0], m))
+        self._check(lib().rb_error_coefficients(self._h, mu.shape[0], _ptr(mu), _ptr(X), _ptr(Z),
+                                                C.c_void_p(int(stream) if stream else 0)))
+        return Z
+
+    def warm_start_error(self, mu, x, net: Optional[Mlp] = None, z=None, stream: Optional[int] = None) -> int:
+        """rb_warm_start_error: x [B][N_dof] = x_hat(mu) + V z, z from the network or given."""
+        mu = _f64(mu).reshape(-1, self.n_mu)
+        zz = None if z is None else (_f64(z) if isinstance(z, np.ndarray) else z)
+        return self._check(lib().rb_warm_start_error(self._h, net.handle if net is not None else None, mu.shape[0],
+                                                     _ptr(mu), _ptr(x), _ptr(zz),
+                                                     C.c_void_p(int(stream) if stream else 0)))
 
     def coefficients(self, x, coef=None, stream: Optional[int] = None):
         """rb_coefficients: W^T x_b for x [B][N_dof] (host or device); returns coef (host unless given)."""

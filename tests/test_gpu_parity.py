@@ -564,3 +564,26 @@ def test_ragged_batch_matches_single_context_solves():
                 assert _rel(xs[c][b].cpu().numpy(), truths[c][b]) < 1e-9
     for ctx in ctxs:
         ctx.close()
+
+
+def test_multi_fidelity_build_matches_oracle():
+    """rb_offline_build_mf (Section 4.2, last paragraph): the GPU greedy on the coarse grid picks
+    the oracle's coarse-grid sample, and the fine basis spans the oracle's fine snapshots of it."""
+    fine = wl.small((24, 20, 16), (2, 2, 2), n_basis=5, n_train=24)
+    coarse = wl.small((12, 10, 8), (2, 2, 2), n_basis=5, n_train=24)
+    train = fine.train_mu()
+    ref = greedy.multi_fidelity(fine.problem, coarse.problem, train, 5)
+    ctx = rb.Context.build_multi_fidelity(fine.problem, coarse.problem, 5, train, max_batch=2)
+    W, ANq, fNr, Rs, sel = ctx.basis()
+    assert [int(s) for s in sel] == ref.selected
+    assert np.abs(W.T @ W - np.eye(W.shape[1])).max() < 1e-12
+    signs = np.sign(np.sum(W * ref.W, axis=0))
+    assert np.abs(W * signs - ref.W).max() < 1e-8
+    # the fine basis solves the fine problem
+    mu = fine.test_mu(2)
+    x = torch.zeros((2, fine.problem.n_dof), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu, x, precision="mixed")
+    assert status == rb.RB_OK
+    for b in range(2):
+        assert _rel(x[b].cpu().numpy(), direct.sparse_direct(fine.problem, mu[b])) < 1e-9
+    ctx.close()

@@ -173,3 +173,86 @@ def test_learned_warm_start_reaches_truth_and_reports_gain():
     assert its["learned"] <= its["cold"] + 1.0
     net.close()
     ctx.close()
+
+
+def test_error_basis_matches_oracle():
+    """rb_error_basis (method of snapshots on the device) against the oracle's POD: the same
+    singular values, the same targets Z = V^T E up to the sign of each mode; rb_error_coefficients
+    reproduces Z; with as many modes as snapshots x_hat + V z_s is the training solution itself."""
+    from oracle import errbasis
+    w = wl.small((40, 36), (3, 3), n_basis=6, n_train=30, bumps=True)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    S = 24
+    mus = wl.mlp_train_mu(w, S)
+    X = np.stack([direct.sparse_direct(prob, m) for m in mus])
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=S)
+    m = 5
+    Zg, sg = ctx.error_basis(mus, X, m)
+    Vo, Zo, so = errbasis.error_basis(basis, mus, X, m)
+    np.testing.assert_allclose(sg, so, rtol=1e-8)
+    signs = np.sign(np.sum(Zg.T * Zo, axis=1))
+    np.testing.assert_allclose(Zg * signs[None, :], Zo.T, rtol=0, atol=1e-7 * np.abs(Zo).max())
+    Xd = torch.as_tensor(X, device="cuda")
+    Zc = ctx.error_coefficients(mus, Xd, m)
+    np.testing.assert_allclose(Zc, Zg, rtol=0, atol=1e-5 * np.abs(Zg).max())
+    # the start from given coefficients equals the oracle's x_hat + V z
+    x0 = np.zeros((S, prob.n_dof))
+    ctx.warm_start_error(mus, x0, z=Zg)
+    for s in (0, 7, 23):
+        ref = errbasis.warm_start(basis, Vo * signs[None, :], mus[s], Zg[s])
+        assert _rel(x0[s], ref) < 1e-6, s
+    # full rank: the training solutions come back
+    Zf, _ = ctx.error_basis(mus, Xd, S)
+    xf = torch.zeros((S, prob.n_dof), dtype=torch.float64, device="cuda")
+    ctx.warm_start_error(mus, xf, z=Zf)
+    for s in range(S):
+        assert _rel(xf[s].cpu().numpy(), X[s]) < 1e-6, s
+    ctx.close()
+
+
+def test_error_basis_warm_start_reaches_truth_and_reports_gain():
+    """3D 24^3, P = 8, n = 12: an error basis of 128 truth solves (m = 16) and a network for its
+    coefficients trained on 512 pairs; the start x_hat + V z(mu) leaves span(W).  Every start reaches
+    the truth; the test reports the initial error and the iterations of each start."""
+    w = wl.small((24, 24, 24), (2, 2, 2), n_basis=12, n_train=96)
+    prob = w.problem
+    S, T, m, Sp = 512, 48, 16, 128
+    ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=S)
+    mu_tr = wl.mlp_train_mu(w, S)
+    x_tr = torch.zeros((S, prob.n_dof), dtype=torch.float64, device="cuda")
+    status, _ = ctx.pcg(mu_tr, x_tr, precision="mixed")
+    assert status == rb.RB_OK
+    Z0, sig = ctx.error_basis(mu_tr[:Sp], x_tr[:Sp], m)
+    assert sig[0] > 0 and np.all(np.diff(sig) <= 1e-12 * sig[0])
+    Z = ctx.error_coefficients(mu_tr, x_tr, m)
+    np.testing.assert_allclose(Z[:Sp], Z0, rtol=0, atol=1e-5 * np.abs(Z0).max())
+    sizes = wl.mlp_layer_sizes(prob.n_mu, m)
+    net = rb.Mlp(prob.n_mu, prob.P, sizes[1], m, rb.flatten_params(wl.mlp_init(sizes)), max_samples=S)
+    hist = net.fit(mu_tr, Z, 1500, lr=3e-3)
+    assert hist[-1] < 0.1 * hist[0], (hist[0], hist[-1])
+    mu = w.test_mu(T)
+    truth = np.stack([direct.sparse_direct(prob, mm) for mm in mu[:4]])
+    runs = {}
+    for name in ("cold", "galerkin", "error_basis"):
+        x = torch.zeros((T, prob.n_dof), dtype=torch.float64, device="cuda")
+        if name == "galerkin":
+            ctx.warm_start(mu, x)
+        elif name == "error_basis":
+            ctx.warm_start_error(mu, x, net=net)
+        x0 = x.cpu().numpy()
+        status, st = ctx.pcg(mu, x, precision="mixed", x0=name != "cold")
+        assert status == rb.RB_OK and np.all(st["rel_res"] < 1e-10), name
+        xs = x.cpu().numpy()
+        for b in range(4):
+            assert _rel(xs[b], truth[b]) < 1e-9, (name, b)
+        runs[name] = (x0, xs, st)
+    ref = runs["cold"][1]
+    err0 = {k: float(np.mean([_rel(v[0][b], ref[b]) for b in range(T)])) for k, v in runs.items()}
+    its = {k: float(v[2]["iters"].mean()) for k, v in runs.items()}
+    print("\nerror-basis warm start, 24^3 P=8 n=12 m=16: mean initial error %s; mean inner iterations %s"
+          % (err0, its))
+    # the error basis removes most of the Galerkin error
+    assert err0["error_basis"] < 0.5 * err0["galerkin"]
+    net.close()
+    ctx.close()

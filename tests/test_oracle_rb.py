@@ -282,3 +282,27 @@ def test_stored_oracle_solves_and_the_restart_policy():
                 assert rb_ == 0 and a == b
             assert b >= a or rb_ > 0
     assert all(r < 1e-10 for r in g["rel_res"] + g["rel_res_nu6"]) and all(g["converged"])
+
+
+def test_multi_fidelity_sample_from_the_coarse_grid():
+    """Section 4.2, last paragraph: the parameter sample comes from the greedy on the coarse grid
+    and the fine basis holds the fine snapshots of that sample.  With the coarse grid equal to the
+    fine one the construction is the plain greedy of Alg. 1."""
+    fine = wl.small((24, 20), (2, 2), n_basis=5, n_train=30, bumps=True)
+    coarse = wl.small((12, 10), (2, 2), n_basis=5, n_train=30, bumps=True)
+    train = fine.train_mu()
+    assert np.array_equal(train, coarse.train_mu())
+    B = greedy.multi_fidelity(fine.problem, coarse.problem, train, 5)
+    Bc = greedy.greedy(coarse.problem, train, 5)
+    assert B.selected == Bc.selected
+    X = np.stack([direct.sparse_direct(fine.problem, train[j]) for j in B.selected], axis=1)
+    assert np.abs(B.W.T @ B.W - np.eye(B.N)).max() < 1e-13
+    assert np.linalg.norm(B.W @ B.R - X) <= 1e-11 * np.linalg.norm(X)
+    for q in range(fine.problem.P):
+        e = np.zeros(fine.problem.n_mu); e[q] = 1.0
+        Aq = pins.incidence_operator(fine.problem.dims, fine.problem.blocks, e)
+        assert np.abs(B.ANq[q] - B.W.T @ Aq @ B.W).max() <= 1e-12 * np.abs(B.ANq[q]).max()
+    same = greedy.multi_fidelity(fine.problem, fine.problem, train, 5)
+    plain = greedy.greedy(fine.problem, train, 5)
+    assert same.selected == plain.selected
+    np.testing.assert_array_equal(same.W, plain.W)
