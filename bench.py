@@ -39,9 +39,20 @@ BYTES_PER_POINT = {
             "outer_residual": 12, "outer_update": 24},
     "f64": {"cg_a": 24, "cg_b": 40, "smooth": 32, "project": 8, "prolong": 8, "outer_residual": 16},
 }
-# Bytes per point of one streaming pass of a red-black sweep before the last (source, r, output):
-# the smoother that runs one pass per sweep moves this much more per extra sweep.
+# Bytes per point of one streaming pass over memory before the last (source, r, output): the
+# smoother moves this much more per extra pass.  kernels 0 and 2 make one pass per sweep, 1 one
+# pass for all sweeps, 3 and 4 one pass per three and per two sweeps.
 SWEEP_PASS_BYTES = {"f32": 12, "f64": 24}
+
+
+def smoother_passes(kernels, nu):
+    """Passes over memory of one 2D smoother application."""
+    if kernels == 1:
+        return 1
+    if kernels in (3, 4):
+        nf = 3 if kernels == 3 else 2
+        return (nu + nf - 1) // nf
+    return nu
 # With BF16 storage of the preconditioner's intermediate vectors: the prolongation writes 2 B;
 # a pass before the last reads source (2) and r (4) and writes 2; the last reads source (2), r (4),
 # p (4) and writes y (4).
@@ -74,6 +85,9 @@ def parse(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=60,
                     help="reference arm: Alg. 3 iterations per core and step (about 10 s of oracle work)")
     ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")
+    ap.add_argument("--mf-coarse", type=int, default=0,
+                    help="build the basis by the multi-fidelity greedy: sample selected on this many nodes per "
+                         "direction, snapshots on the workload's grid (0: plain greedy on the workload's grid)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --nu, --gemm as given)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no per-kernel pass, e2e, FP64 comparator or CPU baseline); for profilers")
@@ -480,11 +494,12 @@ def kernel_table(prof, prec, opts, N, iters, outers):
             entry["alg_bytes_per_point"] = bpp
             entry["gbs"] = round(alg / (ms / 1000.0) / 1e9, 1)
             if k == "smooth":
-                # the streaming passes of the one-pass-per-sweep smoother, nu per application
+                # the streaming passes over memory of one application
                 if bf16:
                     pas = BF16_SMOOTH_LAST + BF16_SMOOTH_SWEEP * (nu - 1)
                 else:
-                    pas = bpp + SWEEP_PASS_BYTES[prec] * (nu - 1)
+                    passes = smoother_passes(opts.get("kernels", 0), nu) if prec == "f32" else nu
+                    pas = bpp + SWEEP_PASS_BYTES[prec] * (passes - 1)
                 entry["pass_bytes_per_point"] = pas
                 entry["pass_gbs"] = round(pas * N * units[k] / (ms / 1000.0) / 1e9, 1)
         kernels[k] = entry
@@ -542,8 +557,14 @@ def main():
     if args.basis and os.path.exists(args.basis):
         ctx = rb.Context.load(args.basis, max_batch=B)
     else:
-        ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B, precision="mixed",
-                               stream=torch.cuda.current_stream(dev).cuda_stream)
+        if args.mf_coarse > 0:
+            import dataclasses
+            coarse = dataclasses.replace(prob, dims=(args.mf_coarse,) * prob.dim)
+            ctx = rb.Context.build_multi_fidelity(prob, coarse, w.n_basis, w.train_mu(), max_batch=B,
+                                                  precision="mixed")
+        else:
+            ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B, precision="mixed",
+                                   stream=torch.cuda.current_stream(dev).cuda_stream)
         if args.basis:
             ctx.save(args.basis)
     offline_s = time.perf_counter() - t0

@@ -92,7 +92,8 @@ typedef struct {
                               nu <= 6);
                            2: CG body and one smoother pass per sweep with rows held in registers;
                            3: as 0, but up to three red-black sweeps per pass over memory (FP32
-                              mixed path with FP32 storage; other cases as 0).
+                              mixed path with FP32 storage; other cases as 0);
+                           4: as 3 with up to two sweeps per pass.
                            On 3D grids (RBCG): 0 marches the CG body and the red-black smoother in
                            z with planes prefetched into shared memory by asynchronous copies;
                            1 the smoother marching in z with direct loads and the generic CG

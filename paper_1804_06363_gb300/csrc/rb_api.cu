@@ -617,8 +617,9 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic &&
                 use_fused_smoother(ctx->geo, o.nu))
                 launch2d_smooth_fused(P, L, o.nu);
-            else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 3 && !P.ybf16 && use_multi_smoother(ctx->geo))
-                launch2d_smooth_multi(P, L, o.nu);
+            else if (rm && o.smoother == RB_SMOOTH_RBGS && (o.kernels == 3 || o.kernels == 4) && !P.ybf16 &&
+                     use_multi_smoother(ctx->geo))
+                launch2d_smooth_multi(P, L, o.nu, o.kernels == 3 ? 3 : 2);
             else if (rm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 && use_tma_smoother(ctx->geo))
                 launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
@@ -644,7 +645,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.nu < 0 || o.max_outer < 1 || !(o.inner_tol > 0.0) ||
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
-        (o.kernels < 0 || o.kernels > 3) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
+        (o.kernels < 0 || o.kernels > 4) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
         (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED) || o.adaptive_n < 0 ||
         !(o.gamma >= 0.0)) {
         ctx->err = "invalid options";
@@ -1229,10 +1230,10 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
         if (best.smoother == RB_SMOOTH_RBGS && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
             !ctx->force_generic) {
             const rb_opts base = best;
-            for (int kk = 0; kk <= 3; ++kk) {
+            for (int kk = 0; kk <= 4; ++kk) {
                 if (kk == base.kernels || (kk == 1 && ctx->geo.dim == 2 && !use_fused_smoother(ctx->geo, base.nu)))
                     continue;
-                if (kk == 3 && (ctx->geo.dim != 2 || !use_multi_smoother(ctx->geo))) continue;
+                if (kk >= 3 && (ctx->geo.dim != 2 || !use_multi_smoother(ctx->geo))) continue;
                 if (kk != 0 && base.store == RB_STORE_BF16) continue;   // BF16 iterates need kernels = 0
                 rb_opts t = base;
                 t.kernels = kk;

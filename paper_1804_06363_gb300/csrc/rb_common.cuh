@@ -353,7 +353,7 @@ template <typename T> void launch2d_smooth_tma(const Params& P, const Launch& L,
 // nu sweeps in passes of up to three, rows staged by bulk asynchronous copies (FP32, dim 2,
 // rows of a multiple of 128 points)
 bool use_multi_smoother(const Geo& g);
-void launch2d_smooth_multi(const Params& P, const Launch& L, int nu);
+void launch2d_smooth_multi(const Params& P, const Launch& L, int nu, int max_nf);
 // all nu sweeps in one pass (FP32, dim 2, mx even, nu <= 6)
 bool use_fused_smoother(const Geo& g, int nu);
 void launch2d_smooth_fused(const Params& P, const Launch& L, int nu);

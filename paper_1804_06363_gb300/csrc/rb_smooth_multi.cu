@@ -39,6 +39,10 @@ using namespace stg;
 namespace {
 
 constexpr int MS_MAX_NF = 3;
+// Steps of one band: its rows plus 2 NH.  A band has at most TB_ROWS rows, since the
+// partial-sum slots (at least one per TILE points) outnumber the bands of 128-point rows.
+constexpr int MS_MAX_STEPS = TB_ROWS + 2 * 2 * MS_MAX_NF;
+static_assert(TILE <= 128 * TB_ROWS, "bands of the multi-sweep smoother would outgrow TB_ROWS");
 
 template <int NF, bool LAST>
 struct MsShape {
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
     __shared__ float mus[MAX_MU];
     __shared__ double red[32];
     __shared__ int s_flag;
+    __shared__ int ukey[MS_MAX_STEPS];   // per step of the item: the common key of the rows in flight, or -1
     const Geo& g = P.g;
     const int mx = MX > 0 ? MX : g.mx, my = g.my;
     const MsLayout<NF, LAST> lay(mx);
@@ -196,6 +201,12 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
         cbar(nthr);   // the previous item no longer reads mus or the edge rows
         for (int j = threadIdx.x; j < P.n_mu; j += nthr) mus[j] = (float)P.mu[(size_t)q * P.n_mu + j];
         for (int i = threadIdx.x; i < NH * 4 * lay.zstride; i += nthr) edge[i] = 0.0f;
+        for (int i = threadIdx.x; i <= klast - kfirst && i < MS_MAX_STEPS; i += nthr) {
+            const int k = kfirst + i;
+            const int kt = min(max(k, 0), my - 1), kb = min(max(k - NH + 1, 0), my - 1);
+            const int a = __ldg(g.rkey + kt), b = __ldg(g.rkey + kb);
+            ukey[i] = a == b ? a : -1;
+        }
         cbar(nthr);
         TCoef<float> cf;   // coefficients of the rows in flight while they share a key
         int ckey = -1;
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
         // one step of the march; PAR = k & 1: every half-sweep updates columns PAR, PAR + 2
         // UNI: the rows k .. k-NH+1 share one key (uniform across the CTA), so every half-sweep
         // uses cf; otherwise each forms its own coefficients
-        auto step = [&](auto par_tag, auto uni_tag, int k) {
+        auto step = [&](auto par_tag, auto uni_tag, int k, int kkey) {
             constexpr int PAR = decltype(par_tag)::value;
             constexpr bool UNI = decltype(uni_tag)::value != 0;
             constexpr int J0 = PAR, J1 = PAR + 2;          // updated columns
@@ -219,11 +230,9 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
             const uint32_t o_cur = cslot * stage_b;
             const uint32_t o_prev = ((cslot + RING_N - 1) % RING_N) * stage_b;
             if constexpr (UNI) {
-                const int kt = min(max(k, 0), my - 1);
-                const int key_t = __ldg(g.rkey + kt);
-                if (key_t != ckey) {
-                    tcoef<float>(g, mus, x0, kt, cf);
-                    ckey = key_t;
+                if (kkey != ckey) {
+                    tcoef<float>(g, mus, x0, min(max(k, 0), my - 1), cf);
+                    ckey = kkey;
                 }
             }
             // ---- H_0: red half-sweep of row k from the old source values
@@ -348,15 +357,13 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
         };
         for (int k = kfirst; k <= klast; k += 2) {
             // rows k .. k-NH+1 (clamped to the grid) share a key: uniform over the CTA
-            auto uniform = [&](int kk) {
-                const int kt = min(max(kk, 0), my - 1), kb = min(max(kk - NH + 1, 0), my - 1);
-                return __ldg(g.rkey + kt) == __ldg(g.rkey + kb);
-            };
-            if (uniform(k)) step(Par1{}, Par1{}, k);
-            else step(Par1{}, Par0{}, k);
+            const int u0 = ukey[k - kfirst];
+            if (u0 >= 0) step(Par1{}, Par1{}, k, u0);
+            else step(Par1{}, Par0{}, k, u0);
             if (k + 1 <= klast) {
-                if (uniform(k + 1)) step(Par0{}, Par1{}, k + 1);
-                else step(Par0{}, Par0{}, k + 1);
+                const int u1 = ukey[k + 1 - kfirst];
+                if (u1 >= 0) step(Par0{}, Par1{}, k + 1, u1);
+                else step(Par0{}, Par0{}, k + 1, u1);
             }
         }
         if (LAST) {
@@ -411,8 +418,9 @@ bool use_multi_smoother(const Geo& g) {
            MsLayout<MS_MAX_NF, true>(g.mx).bytes <= 200u * 1024u;
 }
 
-// nu sweeps in passes of at most 3 (e.g. 6 = 3 + 3, 5 = 3 + 2): ypro -> tmp -> ... -> y
-void launch2d_smooth_multi(const Params& P, const Launch& L, int nu) {
+// nu sweeps in passes of at most max_nf (<= 3; e.g. 6 = 3 + 3, 5 = 3 + 2): ypro -> tmp -> ... -> y
+void launch2d_smooth_multi(const Params& P, const Launch& L, int nu, int max_nf) {
+    max_nf = max_nf < 1 ? 1 : (max_nf > MS_MAX_NF ? MS_MAX_NF : max_nf);
     float* ypro = reinterpret_cast<float*>(P.ypro);
     float* tmp = reinterpret_cast<float*>(P.tmp);
     float* out = reinterpret_cast<float*>(P.y);
@@ -420,7 +428,7 @@ void launch2d_smooth_multi(const Params& P, const Launch& L, int nu) {
     const float* src = ypro;
     bool to_tmp = true;
     while (left > 0) {
-        const int passes = (left + MS_MAX_NF - 1) / MS_MAX_NF;
+        const int passes = (left + max_nf - 1) / max_nf;
         const int nf = (left + passes - 1) / passes;   // spread the sweeps evenly over the passes
         left -= nf;
         if (left == 0) {
