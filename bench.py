@@ -45,6 +45,13 @@ BYTES_PER_POINT = {
 SWEEP_PASS_BYTES = {"f32": 12, "f64": 24}
 
 
+def outer_flops(dim, n_loads):
+    """FP64 operations per point of the outer residual f - A x with its two squared norms: the load
+    sum (one FMA per term), the 5- or 7-point stencil (one FMA per coefficient), the difference and
+    two FMAs for the squares."""
+    return 2 * n_loads + 2 * (2 * dim + 1) + 1 + 4
+
+
 def smoother_passes(kernels, nu):
     """Passes over memory of one 2D smoother application."""
     if kernels == 1:
@@ -476,8 +483,10 @@ def leg_3d(args, dev, stream, peak, peak_kind):
     return out
 
 
-def kernel_table(prof, prec, opts, N, iters, outers):
-    """Per-kernel device time and algorithmic bytes from the rb_profile counters."""
+def kernel_table(prof, prec, opts, N, iters, outers, alu=None):
+    """Per-kernel device time and algorithmic bytes from the rb_profile counters.  alu =
+    (FP64 flops per point of the outer residual, measured FP64 FMA rate in flop/s) adds that
+    kernel's arithmetic roofline."""
     nu = max(1, opts["nu"])
     units = {"cg_a": iters, "cg_b": iters, "smooth": iters, "project": iters, "tc_project": iters,
              "prolong": iters, "tc_prolong": iters, "outer_residual": outers, "outer_update": outers}
@@ -502,6 +511,12 @@ def kernel_table(prof, prec, opts, N, iters, outers):
                     pas = bpp + SWEEP_PASS_BYTES[prec] * (passes - 1)
                 entry["pass_bytes_per_point"] = pas
                 entry["pass_gbs"] = round(pas * N * units[k] / (ms / 1000.0) / 1e9, 1)
+        if k == "outer_residual" and alu is not None and ms > 0:
+            fpp, rate = alu
+            tf = fpp * N * units[k] / (ms / 1000.0) / 1e12
+            entry["fp64_flops_per_point"] = fpp
+            entry["fp64_tflops"] = round(tf, 3)
+            entry["fp64_frac"] = round(tf / (rate / 1e12), 4)
         kernels[k] = entry
     return kernels, units
 
@@ -646,7 +661,10 @@ def main():
     prec = "f32" if args.precision == "mixed" else "f64"
     iters = int(st_prof["iters"].sum())
     outers = int(st_prof["outer"].sum())
-    kernels, units = kernel_table(prof, prec, opts, N, iters, outers)
+    fma64 = rb.fma_rate(True, stream.cuda_stream)   # measured FP64 rate (outside every timed region)
+    fma32 = rb.fma_rate(False, stream.cuda_stream)
+    kernels, units = kernel_table(prof, prec, opts, N, iters, outers,
+                                  alu=(outer_flops(prob.dim, len(prob.loads)), fma64))
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     peak, peak_kind = measured_peaks()
     achieved = kernels[dom].get("gbs")
@@ -666,7 +684,9 @@ def main():
         roofline["per_pass"] = {"bytes_per_point": kernels[dom]["pass_bytes_per_point"],
                                 "achieved": kernels[dom]["pass_gbs"],
                                 "frac": round(kernels[dom]["pass_gbs"] / peak, 4),
-                                "what": f"one streaming pass per red-black sweep ({opts['nu']} per application)"}
+                                "what": "%d streaming passes over memory per application (nu = %d, kernels = %d)"
+                                        % (smoother_passes(opts.get("kernels", 0), opts["nu"]) if prec == "f32"
+                                           else opts["nu"], opts["nu"], opts.get("kernels", 0))}
 
     # ---- end to end through the C interface with host buffers (pinned)
     xh = torch.zeros((B, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -768,6 +788,9 @@ def main():
             "mean_outer": float(last["outer"].mean()), "max_rel_res": float(last["rel_res"].max()),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
             "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu, "parity": parity, "clocks": clocks,
+            "fma_rate": {"fp64_tflops": round(fma64 / 1e12, 3), "fp32_tflops": round(fma32 / 1e12, 2),
+                         "what": "measured by rb_fma_rate on this GPU; denominator of the outer residual's "
+                                 "fp64_frac"},
         }
         if warm is not None:
             line["warm_start"] = warm

@@ -278,6 +278,15 @@ typedef struct {
 rb_status rb_profile(rb_ctx* ctx, int enable);
 rb_status rb_profile_read(const rb_ctx* ctx, rb_kernel_time* out, int cap, int* count);
 
+/* Measured FMA rate of the current device: *flops_per_s = 2 x FMAs per second of a
+ * launch that fills every SM with independent chains of dependent fused multiply-adds
+ * (fp64 = 1: double, 0: float), timed with CUDA events on stream (NULL = legacy default
+ * stream) after one warm-up launch of the same size; about 50-200 ms in all.  It is the
+ * denominator of the roofline of a kernel bound by arithmetic rather than by memory (the
+ * FP64 outer residual of the mixed solver).  Allocates and frees a few MB of device
+ * memory; needs no context.  RB_EINVAL if flops_per_s is NULL. */
+rb_status rb_fma_rate(int fp64, double* flops_per_s, void* stream);
+
 /*
  * Starting vectors.  Alg. 2 and Alg. 3 start from x_0 = 0 but accept any x_0
  * (rb_opts.x0_mode = RB_X0_GIVEN).  rb_warm_start writes x_b = W c_b with

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rb_api.cu", "rb_stencil.cu", "rb_stencil2d.cu", "rb_reduced.cu", "rb_tc.cu", "rb_noalloc.cu", "rb_smooth_fused.cu", "rb_smooth_tma.cu", "rb_cg_tma.cu", "rb_outer_tma.cu", "rb_mlp.cu", "rb_stencil3d.cu", "rb_ztile.cu", "rb_smooth_multi.cu", "rb_errbasis.cu"]
+SOURCES = ["rb_api.cu", "rb_stencil.cu", "rb_stencil2d.cu", "rb_reduced.cu", "rb_tc.cu", "rb_noalloc.cu", "rb_smooth_fused.cu", "rb_smooth_tma.cu", "rb_cg_tma.cu", "rb_outer_tma.cu", "rb_mlp.cu", "rb_stencil3d.cu", "rb_ztile.cu", "rb_smooth_multi.cu", "rb_errbasis.cu", "rb_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcudafe", "--diag_suppress=177"]

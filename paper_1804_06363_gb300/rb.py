@@ -90,6 +90,7 @@ SIGNATURES = {
                               C.POINTER(RbTuneResult)]),
     "rb_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rb_profile_read": (C.c_int, [C.c_void_p, C.POINTER(RbKernelTime), C.c_int, C.POINTER(C.c_int)]),
+    "rb_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "rb_residual_noalloc": (C.c_int, [C.POINTER(RbProblem), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
     "rb_warm_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -212,6 +213,15 @@ def stats_array(st) -> np.ndarray:
     for i in range(n):
         out[i] = (st[i].iters, st[i].outer, st[i].restarts, st[i].status, st[i].rel_res, st[i].n_used)
     return out
+
+
+def fma_rate(fp64: bool = True, stream: Optional[int] = None) -> float:
+    """rb_fma_rate: measured FMA throughput of the current device in flop/s."""
+    out = C.c_double()
+    st = lib().rb_fma_rate(1 if fp64 else 0, C.byref(out), stream)
+    if st != RB_OK:
+        raise RbError(st, "rb_fma_rate failed")
+    return out.value
 
 
 def residual_noalloc(prob, mu, x, stream: Optional[int] = None) -> np.ndarray:
