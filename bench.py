@@ -108,6 +108,9 @@ def parse(argv=None):
     ap.add_argument("--no-leg3d", action="store_true",
                     help="skip the 3D leg (128^3, 256 queries per step, timed after the 2D results)")
     ap.add_argument("--leg3d-steps", type=int, default=2)
+    ap.add_argument("--n-sweep", default="",
+                    help="comma-separated basis sizes: steps of RBI and RBCG versus N on the workload's test "
+                         "parameters (the paper's steps-versus-RB-dimension study) instead of the timed bench")
     ap.add_argument("--rank-check", action="store_true",
                     help="CPU only: start the ranks, shard the queries and agree on the max time over gloo")
     return ap.parse_args(argv)
@@ -422,6 +425,53 @@ def warm_start_experiment(ctx, w, args, opts, dev, stream):
     return out
 
 
+def n_sweep(args, w, ctx, dev, stream):
+    """Steps to relative residual 1e-10 of RBI (Alg. 2) and RBCG (Alg. 3, FP64, PR beta) versus the
+    basis size N, on the workload's test parameters, with the leading N vectors of one greedy basis
+    (the greedy's bases are nested).  Per N: mean, best and worst step counts and their mid-range
+    (the paper's Fig. 5 plots the average of the best and the worst case), and the throughput of
+    the mixed-precision RBCG on the same queries."""
+    prob = w.problem
+    sizes = [int(t) for t in args.n_sweep.split(",") if t.strip()]
+    W, ANq, fNr, _, _ = ctx.basis()
+    mu = w.test_mu()
+    B = len(mu)
+    x = torch.zeros((B, prob.n_dof), dtype=torch.float64, device=dev)
+    rows = []
+
+    def summary(st):
+        it = st["iters"].astype(np.int64)
+        return {"mean": float(it.mean()), "best": int(it.min()), "worst": int(it.max()),
+                "mid_range": 0.5 * float(it.min() + it.max()),
+                "converged": int(np.sum(st["status"] == rb.RB_OK))}
+
+    for n in sizes:
+        c = rb.Context.from_arrays(prob, W[:, :n], ANq[:, :n, :n], fNr[:, :n], max_batch=B)
+        x.zero_()
+        _, st_rbi = c.solve(mu, x, max_iter=20000, stream=stream.cuda_stream)
+        x.zero_()
+        _, st_cg = c.pcg(mu, x, precision="fp64", beta="pr", max_iter=5000, stream=stream.cuda_stream)
+        x.zero_()
+        c.pcg(mu, x, precision="mixed", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x.zero_()
+        e0.record(stream)
+        _, st_mx = c.pcg(mu, x, precision="mixed", stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows.append({"N": n, "rbi_steps": summary(st_rbi), "rbcg_steps": summary(st_cg),
+                     "rbcg_mixed": {"solves_per_s": round(B / (e0.elapsed_time(e1) / 1000.0), 1),
+                                    "mean_inner_iters": float(st_mx["iters"].mean()),
+                                    "converged": int(np.sum(st_mx["status"] == rb.RB_OK))}})
+        progress(f"N = {n}: RBI {rows[-1]['rbi_steps']['mid_range']}, RBCG {rows[-1]['rbcg_steps']['mid_range']} "
+                 f"(mid-range of best and worst steps)")
+        c.close()
+    return {"metric": "steps to rel. residual 1e-10 versus RB dimension N", "workload": w.name,
+            "grid": "x".join(map(str, prob.dims)), "queries": B, "smoother": "red-black GS nu=1",
+            "data": "synthetic", "n_sweep": rows}
+
+
 def leg_3d(args, dev, stream, peak, peak_kind):
     """The 3D workload (128^3, P = 8, n = 60, 256 queries per step) on the same GPU after the 2D
     results: basis built by the GPU greedy (snapshots by mixed-precision RBCG to 1e-11), the
@@ -578,13 +628,19 @@ def main():
             ctx = rb.Context.build_multi_fidelity(prob, coarse, w.n_basis, w.train_mu(), max_batch=B,
                                                   precision="mixed")
         else:
-            ctx = rb.Context.build(prob, w.n_basis, w.train_mu(), max_batch=B, precision="mixed",
+            n_build = max([w.n_basis] + [int(t) for t in args.n_sweep.split(",") if t.strip()])
+            ctx = rb.Context.build(prob, n_build, w.train_mu(), max_batch=B, precision="mixed",
                                    stream=torch.cuda.current_stream(dev).cuda_stream)
         if args.basis:
             ctx.save(args.basis)
     offline_s = time.perf_counter() - t0
     progress(f"basis of {w.name} ready in {offline_s:.1f} s")
     _, _, _, _, sel = ctx.basis()
+    if args.n_sweep:
+        if rank == 0:
+            print(json.dumps(n_sweep(args, w, ctx, dev, torch.cuda.current_stream(dev))))
+        ctx.close()
+        return 0
 
     # weak scaling: every rank solves its own B test parameters (replicas, no data-path collective)
     from paper_1804_06363_gb300.shard import max_over_ranks, shard_range

@@ -10,6 +10,12 @@
  * of a box partition, block of node i_d is floor(i_d * nb_d / m_d); a face
  * between two nodes carries (mu_p(i) + mu_p(j))/2, a face to the boundary
  * mu_p(i).  Theta_q(mu) = mu_q, Q = P = nb_x nb_y nb_z.
+ * With coefficient fields (rb_problem.n_fields = Q > 0; the paper's Section 5
+ * cases) the node coefficient is kappa(i) = sum_q mu_q F_q(i) with given node
+ * values F_q and the same face rule, so A(mu) = sum_q mu_q A_q still holds.
+ * Non-zero Dirichlet data enter as load terms (RB_LOAD_BOUNDARY): the face of
+ * node i to boundary node j carries kappa(i), so g(j) moves to the right-hand
+ * side as sum_q mu_q F_q(i) g(j) / h_d^2, one load term per field.
  *
  * Conventions for every call:
  *  - Vectors of a batch are [B][N_dof] doubles, query-major, x fastest.
@@ -47,21 +53,35 @@ typedef enum {
 } rb_status;
 
 /* One load term f_r of f(mu) = sum_r Phi_r(mu) f_r (eq. 12). */
-enum { RB_LOAD_CONST = 0, RB_LOAD_GAUSS = 1 };
+enum { RB_LOAD_CONST = 0, RB_LOAD_GAUSS = 1, RB_LOAD_ARRAY = 2, RB_LOAD_BOUNDARY = 3 };
 typedef struct {
-    int kind;           /* RB_LOAD_CONST: f_r = 1; RB_LOAD_GAUSS: exp(-|x-c|^2/(2 sigma^2)) */
+    int kind;           /* RB_LOAD_CONST: f_r = 1; RB_LOAD_GAUSS: exp(-|x-c|^2/(2 sigma^2));
+                           RB_LOAD_ARRAY: f_r(i) = values[i] ([N_dof]);
+                           RB_LOAD_BOUNDARY: the lift of Dirichlet data g through field
+                           `field`: f_r(i) = sum over the faces of node i to a boundary node j
+                           of F_field(i) g(j) / h_d^2, with g = values on the grid extended by
+                           the boundary layer ([m_z+2][m_y+2][m_x+2], x fastest; 2D:
+                           [m_y+2][m_x+2]; only the boundary layer is read).  In a block
+                           problem F_q is the indicator of block q. */
     int param;          /* -1: Phi_r = 1; otherwise Phi_r(mu) = mu[param] */
     double center[3];
     double sigma;
+    int field;          /* RB_LOAD_BOUNDARY: q in 0..Q-1 */
+    const double* values;   /* RB_LOAD_ARRAY / RB_LOAD_BOUNDARY: host memory, copied when a
+                               context is created (NULL for the other kinds) */
 } rb_load;
 
 typedef struct {
     int dim;            /* 2 or 3 */
     int m[3];           /* interior nodes per direction; m[2] = 1 when dim = 2 */
-    int nb[3];          /* blocks per direction; nb[2] = 1 when dim = 2 */
+    int nb[3];          /* blocks per direction; nb[2] = 1 when dim = 2; all 1 with fields */
     int n_loads;        /* R >= 1 */
     const rb_load* loads;
     int n_mu;           /* entries of one parameter vector (>= P and > every load param) */
+    int n_fields;       /* 0: block coefficients; Q >= 1: coefficient fields, P = Q */
+    const double* fields;   /* [Q][N_dof] node values F_q (host, copied when a context is created;
+                               NULL when n_fields = 0).  Field problems run the generic stencil
+                               kernels (rb_opts.kernels is ignored). */
 } rb_problem;
 
 enum { RB_SMOOTH_NONE = 0, RB_SMOOTH_RBGS = 1, RB_SMOOTH_JACOBI = 2 };
@@ -411,6 +431,8 @@ void rb_mlp_free(rb_mlp* net);
  * holds the device memory, or latency-bound code that cannot accept the
  * device-wide synchronisation an allocation may cause.  It needs no rb_ctx.
  *   prob     the problem, checked as for rb_offline_load_arrays (RB_EINVAL);
+ *            block coefficients and RB_LOAD_CONST / RB_LOAD_GAUSS loads only (field
+ *            problems and array or boundary loads need a context: RB_EINVAL);
  *   mu       host [B][n_mu];   x  device [B][N_dof] of the current device
  *            (host memory and another device's memory are rejected, RB_EINVAL);
  *   rel_res  host [B], written; stream as in rb_opts (may be NULL).

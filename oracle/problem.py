@@ -14,6 +14,15 @@ elements, Section 5):
     A(mu) = sum_p mu_p A_p affine in mu (eq. 12 with Theta_q(mu) = mu_q, Q = P).
   * f(mu) = sum_r phi_r(mu) f_r (eq. 12), phi_r = 1 or mu[param_r];
     f_r = 1 (const) or exp(-|x - c_r|^2 / (2 sigma_r^2)) at the nodes.
+  * Coefficient fields (the paper's Section 5 cases): the node coefficient is
+    kappa(i) = sum_q mu_q F_q(i) with given node values F_q, the face rule is the
+    same, so A(mu) = sum_q mu_q A_q with A_q the operator of kappa = F_q.
+  * Non-zero Dirichlet data g (the paper's Case 2): in the row of a node i next
+    to the boundary, the face to the boundary node j carries kappa(i) and the
+    known value g(j) moves to the right-hand side, kappa(i) g(j) / h_d^2.  With
+    kappa = sum_q mu_q F_q the lift is affine: a "boundary" load term is
+    sum over the boundary faces of F_q(i) g(j) / h_d^2 for one field q.
+    (In block problems F_q is the indicator of block q.)
 """
 from __future__ import annotations
 
@@ -48,10 +57,25 @@ def node_block(prob: Problem) -> np.ndarray:
     return p
 
 
+def node_fields(prob: Problem) -> np.ndarray:
+    """[P][grid] the fields F_q at the nodes: the given fields, or the block indicators."""
+    F = prob.field_values()
+    if F is not None:
+        return np.asarray(F, dtype=np.float64).reshape((prob.P,) + grid_shape(prob))
+    blk = node_block(prob)
+    return np.stack([(blk == q).astype(np.float64) for q in range(prob.P)])
+
+
 def node_coefficient(prob: Problem, mu) -> np.ndarray:
-    """kappa at every node: mu_p(i) (grid-shaped)."""
+    """kappa at every node (grid-shaped): mu_p(i) on blocks, sum_q mu_q F_q(i) with fields."""
     mu = np.asarray(mu, dtype=np.float64)
-    return mu[:prob.P][node_block(prob)]
+    if prob.coefficient == "blocks":
+        return mu[:prob.P][node_block(prob)]
+    F = node_fields(prob)
+    K = np.zeros(grid_shape(prob))
+    for q in range(prob.P):
+        K += mu[q] * F[q]
+    return K
 
 
 def _sl(ndim, ax, s):
@@ -151,12 +175,36 @@ def node_coordinates(prob: Problem):
     return coords
 
 
+def boundary_lift(prob: Problem, F, G) -> np.ndarray:
+    """sum over the boundary faces of node i of F(i) g(j) / h_d^2 (flat), with F grid-shaped
+    and G the Dirichlet data on the grid extended by the boundary layer (shape + 2 per axis)."""
+    nd = prob.dim
+    out = np.zeros(grid_shape(prob))
+    inner = tuple(slice(1, -1) for _ in range(nd))
+    for d in range(nd):
+        ax = nd - 1 - d
+        m = prob.dims[d]
+        inv_h2 = float(m + 1) ** 2
+        for node, ghost in ((0, 0), (m - 1, m + 1)):
+            sel = list(inner)
+            sel[ax] = slice(ghost, ghost + 1)
+            g = G[tuple(sel)]                               # boundary nodes facing this layer
+            lay = _sl(nd, ax, slice(node, node + 1))
+            out[lay] += F[lay] * g * inv_h2
+    return out.reshape(-1)
+
+
 def load_term(prob: Problem, r: int) -> np.ndarray:
     """f_r at the nodes (flat)."""
     ld = prob.loads[r]
     shape = grid_shape(prob)
     if ld.kind == "const":
         return np.ones(prob.n_dof)
+    if ld.kind == "array":
+        return np.asarray(prob.load_values(r), dtype=np.float64).copy()
+    if ld.kind == "boundary":
+        G = np.asarray(prob.load_values(r), dtype=np.float64).reshape(tuple(s + 2 for s in shape))
+        return boundary_lift(prob, node_fields(prob)[ld.field], G)
     coords = node_coordinates(prob)
     d2 = np.zeros(shape)
     for d in range(prob.dim):

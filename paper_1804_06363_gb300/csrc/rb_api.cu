@@ -48,6 +48,10 @@ PtrKind pointer_kind(const void* p) {
 rb_status validate_problem(const rb_problem* prob, std::string& why) {
     if (!prob) { why = "problem is NULL"; return RB_EINVAL; }
     if (prob->dim != 2 && prob->dim != 3) { why = "dim must be 2 or 3"; return RB_EINVAL; }
+    if (prob->n_fields < 0 || prob->n_fields > MAX_P || (prob->n_fields > 0 && !prob->fields)) {
+        why = "n_fields must be in 0..64, with a field array when positive";
+        return RB_EINVAL;
+    }
     long long P = 1;
     for (int d = 0; d < 3; ++d) {
         if (prob->m[d] < 1 || prob->nb[d] < 1 || prob->nb[d] > prob->m[d]) {
@@ -58,14 +62,23 @@ rb_status validate_problem(const rb_problem* prob, std::string& why) {
     }
     if (prob->dim == 2 && (prob->m[2] != 1 || prob->nb[2] != 1)) { why = "dim 2 needs m[2] = nb[2] = 1"; return RB_EINVAL; }
     if (P > MAX_P) { why = "too many blocks (max 64)"; return RB_EINVAL; }
+    if (prob->n_fields > 0) {
+        if (P != 1) { why = "a problem with coefficient fields has one block per direction"; return RB_EINVAL; }
+        P = prob->n_fields;
+    }
     if ((long long)prob->m[0] * prob->m[1] * prob->m[2] >= (1LL << 31)) { why = "grid too large (N_dof >= 2^31)"; return RB_EINVAL; }
     if (prob->n_loads < 1 || prob->n_loads > MAX_LOADS || !prob->loads) { why = "need 1..8 load terms"; return RB_EINVAL; }
     if (prob->n_mu < P || prob->n_mu > MAX_MU) { why = "n_mu must be in P..128"; return RB_EINVAL; }
     for (int r = 0; r < prob->n_loads; ++r) {
         const rb_load& l = prob->loads[r];
-        if (l.kind != RB_LOAD_CONST && l.kind != RB_LOAD_GAUSS) { why = "unknown load kind"; return RB_EINVAL; }
+        if (l.kind < RB_LOAD_CONST || l.kind > RB_LOAD_BOUNDARY) { why = "unknown load kind"; return RB_EINVAL; }
         if (l.param >= prob->n_mu || l.param < -1) { why = "load parameter index out of range"; return RB_EINVAL; }
         if (l.kind == RB_LOAD_GAUSS && !(l.sigma > 0.0)) { why = "Gaussian load needs sigma > 0"; return RB_EINVAL; }
+        if (l.kind >= RB_LOAD_ARRAY && !l.values) { why = "array and boundary loads need values"; return RB_EINVAL; }
+        if (l.kind == RB_LOAD_BOUNDARY && (l.field < 0 || l.field >= P)) {
+            why = "boundary load field index out of range";
+            return RB_EINVAL;
+        }
     }
     return RB_OK;
 }
@@ -76,8 +89,13 @@ struct rb_ctx {
     // problem
     int dim = 2, m[3] = {1, 1, 1}, nbk[3] = {1, 1, 1}, P = 1, R = 1, n_mu = 1;
     long long N = 0;
-    std::vector<rb_load> loads;
+    std::vector<rb_load> loads;                 // values point into load_vals
+    std::vector<std::vector<double>> load_vals; // copies of the array / boundary loads' values
     int load_param[MAX_LOADS] = {0};
+    int n_fields = 0;                           // coefficient fields (0: blocks)
+    std::vector<double> h_fields;               // [Q][N] copy of the fields
+    double* d_kf64 = nullptr;
+    float* d_kf32 = nullptr;
     Geo geo{};
     int *d_bx = nullptr, *d_by = nullptr, *d_bz = nullptr, *d_rkey = nullptr;
     double* d_fr = nullptr;
@@ -202,14 +220,67 @@ bool is_device_ptr(rb_ctx* ctx, const void* p, bool* bad) {
 int pad_to(int v, int m) { return ((v + m - 1) / m) * m; }
 
 // Allocate everything of a context for basis capacity n_cap and batch Bmax.
+// f(i) = sum over the faces of node i to a boundary node j of F_q(i) g(j) / h_d^2 (the lift of the
+// Dirichlet data g through field q); g on the grid extended by the boundary layer, x fastest.  In a
+// block problem F_q is the indicator of block q.
+void boundary_lift(const rb_ctx* ctx, int q, const double* gext, const std::vector<int> (&maps)[3],
+                   std::vector<double>& f) {
+    const int mx = ctx->m[0], my = ctx->m[1], mz = ctx->m[2], d3 = ctx->dim == 3;
+    const long long N = ctx->N;
+    f.assign(N, 0.0);
+    const long long ex = mx + 2, exy = ex * (my + 2);
+    auto G = [&](int ex_, int ey_, int ez_) { return gext[ex_ + ex * ey_ + exy * (d3 ? ez_ : 0)]; };
+    auto F = [&](int ix, int iy, int iz) -> double {
+        const long long i = ix + (long long)mx * (iy + (long long)my * iz);
+        if (ctx->n_fields > 0) return ctx->h_fields[(size_t)q * N + i];
+        const int p = maps[0][ix] + ctx->nbk[0] * (maps[1][iy] + ctx->nbk[1] * maps[2][iz]);
+        return p == q ? 1.0 : 0.0;
+    };
+    const double ihx2 = (double)(mx + 1) * (mx + 1), ihy2 = (double)(my + 1) * (my + 1),
+                 ihz2 = (double)(mz + 1) * (mz + 1);
+    for (int iz = 0; iz < mz; ++iz)
+        for (int iy = 0; iy < my; ++iy)
+            for (int ix = 0; ix < mx; ++ix) {
+                const bool bx0 = ix == 0, bx1 = ix == mx - 1, by0 = iy == 0, by1 = iy == my - 1;
+                const bool bz0 = d3 && iz == 0, bz1 = d3 && iz == mz - 1;
+                if (!(bx0 || bx1 || by0 || by1 || bz0 || bz1)) continue;
+                const int ez = iz + 1;   // extended-grid indices of the node
+                double s = 0.0;
+                if (bx0) s += ihx2 * G(0, iy + 1, ez);
+                if (bx1) s += ihx2 * G(mx + 1, iy + 1, ez);
+                if (by0) s += ihy2 * G(ix + 1, 0, ez);
+                if (by1) s += ihy2 * G(ix + 1, my + 1, ez);
+                if (bz0) s += ihz2 * G(ix + 1, iy + 1, 0);
+                if (bz1) s += ihz2 * G(ix + 1, iy + 1, mz + 1);
+                f[ix + (long long)mx * (iy + (long long)my * iz)] = F(ix, iy, iz) * s;
+            }
+}
+
 rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch) {
     ctx->dim = prob->dim;
     for (int d = 0; d < 3; ++d) { ctx->m[d] = prob->m[d]; ctx->nbk[d] = prob->nb[d]; }
-    ctx->P = prob->nb[0] * prob->nb[1] * prob->nb[2];
+    ctx->n_fields = prob->n_fields;
+    ctx->P = prob->n_fields > 0 ? prob->n_fields : prob->nb[0] * prob->nb[1] * prob->nb[2];
     ctx->R = prob->n_loads;
     ctx->n_mu = prob->n_mu;
     ctx->N = (long long)prob->m[0] * prob->m[1] * prob->m[2];
     ctx->loads.assign(prob->loads, prob->loads + prob->n_loads);
+    ctx->load_vals.assign(prob->n_loads, std::vector<double>());
+    for (int r = 0; r < ctx->R; ++r) {
+        rb_load& l = ctx->loads[r];
+        if (l.kind == RB_LOAD_ARRAY) {
+            ctx->load_vals[r].assign(l.values, l.values + ctx->N);
+        } else if (l.kind == RB_LOAD_BOUNDARY) {
+            const size_t ext = (size_t)(prob->m[0] + 2) * (prob->m[1] + 2) * (prob->dim == 3 ? prob->m[2] + 2 : 1);
+            ctx->load_vals[r].assign(l.values, l.values + ext);
+        }
+        l.values = l.kind >= RB_LOAD_ARRAY ? ctx->load_vals[r].data() : nullptr;
+        if (l.kind != RB_LOAD_BOUNDARY) l.field = 0;
+    }
+    if (ctx->n_fields > 0) {
+        ctx->h_fields.assign(prob->fields, prob->fields + (size_t)ctx->n_fields * ctx->N);
+        ctx->force_generic = true;   // the staged and tiled kernels take block coefficients only
+    }
     for (int r = 0; r < ctx->R; ++r) ctx->load_param[r] = prob->loads[r].param;
     ctx->n_cap = n_cap;
     ctx->nbp = std::max(16, pad_to(n_cap, 16));
@@ -254,6 +325,17 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
     g.ihy2 = (double)(g.my + 1) * (g.my + 1);
     g.ihz2 = ctx->dim == 3 ? (double)(g.mz + 1) * (g.mz + 1) : 0.0;
     g.bx = ctx->d_bx; g.by = ctx->d_by; g.bz = ctx->d_bz; g.rkey = ctx->d_rkey;
+    if (ctx->n_fields > 0) {
+        const size_t QN = (size_t)ctx->n_fields * N;
+        TRY(dalloc(ctx, &ctx->d_kf64, QN));
+        TRY(dalloc(ctx, &ctx->d_kf32, QN));
+        CK(cudaMemcpy(ctx->d_kf64, ctx->h_fields.data(), QN * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<float> f32(ctx->h_fields.begin(), ctx->h_fields.end());
+        CK(cudaMemcpy(ctx->d_kf32, f32.data(), QN * sizeof(float), cudaMemcpyHostToDevice));
+        g.nf = ctx->n_fields;
+        g.kf64 = ctx->d_kf64;
+        g.kf32 = ctx->d_kf32;
+    }
 
     // load terms
     TRY(dalloc(ctx, &ctx->d_fr, (size_t)ctx->R * N));
@@ -275,6 +357,18 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
         launch_fill_loads(g, ctx->R, dk, dc, ds, ctx->d_fr, ctx->own_stream);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->own_stream));
+        // array loads as given; boundary loads lifted on the host (only the nodes next to the
+        // boundary are non-zero)
+        for (int r = 0; r < ctx->R; ++r) {
+            if (ctx->loads[r].kind == RB_LOAD_ARRAY) {
+                CK(cudaMemcpy(ctx->d_fr + (size_t)r * N, ctx->load_vals[r].data(), N * sizeof(double),
+                              cudaMemcpyHostToDevice));
+            } else if (ctx->loads[r].kind == RB_LOAD_BOUNDARY) {
+                std::vector<double> f;
+                boundary_lift(ctx, ctx->loads[r].field, ctx->load_vals[r].data(), maps, f);
+                CK(cudaMemcpy(ctx->d_fr + (size_t)r * N, f.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+            }
+        }
     }
 
     // basis storage
@@ -1227,7 +1321,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             const double ms = trial(t);
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
-        if (best.smoother == RB_SMOOTH_RBGS && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
+        if (best.smoother == RB_SMOOTH_RBGS && !ctx->force_generic && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
             !ctx->force_generic) {
             const rb_opts base = best;
             for (int kk = 0; kk <= 4; ++kk) {

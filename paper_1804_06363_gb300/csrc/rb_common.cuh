@@ -39,6 +39,9 @@ struct Geo {
     const int* bz;               // [mz]
     const int* rkey;             // [my] block rows of y-rows k-1, k, k+1 packed (0xFF: no row); rows
                                  // with equal keys have equal face coefficients in 2D
+    int nf;                      // coefficient fields (0: block coefficients)
+    const double* kf64;          // [nf][n] node values of the fields
+    const float* kf32;           // the same in FP32
 };
 
 // Per-query phase of the solver state machine.
@@ -141,8 +144,45 @@ struct Coef {
 };
 
 template <typename T>
+__device__ __forceinline__ const T* field_values(const Geo& g);
+template <>
+__device__ __forceinline__ const double* field_values<double>(const Geo& g) { return g.kf64; }
+template <>
+__device__ __forceinline__ const float* field_values<float>(const Geo& g) { return g.kf32; }
+
+// kappa(i) = sum_q mu_q F_q(i) of a problem with coefficient fields
+template <typename T>
+__device__ __forceinline__ T field_kappa(const Geo& g, const T* __restrict__ mus, long long i) {
+    const T* F = field_values<T>(g);
+    T k = T(0);
+    for (int q = 0; q < g.nf; ++q) k += mus[q] * __ldg(F + (size_t)q * g.n + i);
+    return k;
+}
+
+template <typename T>
 __device__ __forceinline__ void node_coef(const Geo& g, const T* __restrict__ mus, int ix, int iy, int iz,
                                           Coef<T>& c) {
+    if (g.nf > 0) {   // coefficient fields: the same face rule on kappa(i) = sum_q mu_q F_q(i)
+        const T half = T(0.5);
+        const T hx = (T)g.ihx2, hy = (T)g.ihy2, hz = (T)g.ihz2;
+        const long long i = ix + (long long)g.mx * (iy + (long long)g.my * iz);
+        const T m = field_kappa(g, mus, i);
+        c.kxm = hx * (ix > 0 ? half * (m + field_kappa(g, mus, i - 1)) : m);
+        c.kxp = hx * (ix < g.mx - 1 ? half * (m + field_kappa(g, mus, i + 1)) : m);
+        c.kym = hy * (iy > 0 ? half * (m + field_kappa(g, mus, i - g.mx)) : m);
+        c.kyp = hy * (iy < g.my - 1 ? half * (m + field_kappa(g, mus, i + g.mx)) : m);
+        T dg = c.kxm + c.kxp + c.kym + c.kyp;
+        if (g.dim == 3) {
+            const long long pl = (long long)g.mx * g.my;
+            c.kzm = hz * (iz > 0 ? half * (m + field_kappa(g, mus, i - pl)) : m);
+            c.kzp = hz * (iz < g.mz - 1 ? half * (m + field_kappa(g, mus, i + pl)) : m);
+            dg += c.kzm + c.kzp;
+        } else {
+            c.kzm = c.kzp = T(0);
+        }
+        c.diag = dg;
+        return;
+    }
     const int bxc = __ldg(g.bx + ix), byc = __ldg(g.by + iy), bzc = __ldg(g.bz + iz);
     const int pyz = g.nbx * (byc + g.nby * bzc);
     const T m = mus[bxc + pyz];

@@ -224,6 +224,12 @@ extern "C" rb_status rb_residual_noalloc(const rb_problem* prob, int B, const do
     if (B < 0 || (B > 0 && (!mu || !x || !rel_res))) { g_na_error = "NULL argument or B < 0"; return RB_EINVAL; }
     std::string why;
     if (rbk::validate_problem(prob, why) != RB_OK) { g_na_error = why; return RB_EINVAL; }
+    bool needs_ctx = prob->n_fields > 0;
+    for (int r = 0; r < prob->n_loads; ++r) needs_ctx |= prob->loads[r].kind >= RB_LOAD_ARRAY;
+    if (needs_ctx) {
+        g_na_error = "coefficient fields and array or boundary loads need a context";
+        return RB_EINVAL;
+    }
     const long long n = (long long)prob->m[0] * prob->m[1] * prob->m[2];
     if (B == 0) return RB_OK;
     for (size_t i = 0; i < (size_t)B * prob->n_mu; ++i)

@@ -331,7 +331,7 @@ rb_status rb_save(const rb_ctx* ctx, const char* path) {
     };
     const int n = ctx->n;
     int32_t hdr[12] = {1, ctx->dim, ctx->m[0], ctx->m[1], ctx->m[2], ctx->nbk[0], ctx->nbk[1], ctx->nbk[2],
-                       ctx->R, ctx->n_mu, n, 0};
+                       ctx->R, ctx->n_mu, n, ctx->n_fields};
     put(RBB_MAGIC, 4);
     put(hdr, sizeof(hdr));
     for (const rb_load& l : ctx->loads) {
@@ -340,6 +340,16 @@ rb_status rb_save(const rb_ctx* ctx, const char* path) {
         put(l.center, sizeof(l.center));
         put(&l.sigma, sizeof(double));
     }
+    // array and boundary loads: field index, value count, values; then the coefficient fields
+    for (int r = 0; r < ctx->R; ++r) {
+        if (ctx->loads[r].kind < RB_LOAD_ARRAY) continue;
+        const int64_t cnt = (int64_t)ctx->load_vals[r].size();
+        const int32_t fld = ctx->loads[r].field;
+        put(&fld, sizeof(fld));
+        put(&cnt, sizeof(cnt));
+        put(ctx->load_vals[r].data(), (size_t)cnt * sizeof(double));
+    }
+    put(ctx->h_fields.data(), ctx->h_fields.size() * sizeof(double));
     put(Wrow.data(), Wrow.size() * sizeof(double));
     put(ctx->h_ANq.data(), ctx->h_ANq.size() * sizeof(double));
     put(ctx->h_fNr.data(), ctx->h_fNr.size() * sizeof(double));
@@ -403,12 +413,46 @@ rb_status rb_offline_load(rb_ctx** out, const char* path, int max_batch) {
         }
         l.kind = kp[0];
         l.param = kp[1];
+        l.field = 0;
+        l.values = nullptr;
+    }
+    const long long N = (long long)prob.m[0] * prob.m[1] * prob.m[2];
+    if (prob.m[0] < 1 || prob.m[1] < 1 || prob.m[2] < 1 || N >= (1LL << 31) || hdr[11] < 0 || hdr[11] > MAX_P) {
+        g_create_error = "basis file header out of range";
+        return RB_EFORMAT;
+    }
+    std::vector<std::vector<double>> lvals(prob.n_loads);
+    for (int r = 0; r < prob.n_loads; ++r) {
+        if (loads[r].kind < RB_LOAD_ARRAY || loads[r].kind > RB_LOAD_BOUNDARY) continue;
+        int32_t fld;
+        int64_t cnt;
+        const long long ext = (long long)(prob.m[0] + 2) * (prob.m[1] + 2) * (prob.dim == 3 ? prob.m[2] + 2 : 1);
+        if (!take(&fld, sizeof(fld)) || !take(&cnt, sizeof(cnt)) ||
+            cnt != (loads[r].kind == RB_LOAD_ARRAY ? N : ext)) {
+            g_create_error = "truncated or inconsistent load values in basis file";
+            return RB_EFORMAT;
+        }
+        lvals[r].resize((size_t)cnt);
+        if (!take(lvals[r].data(), (size_t)cnt * sizeof(double))) {
+            g_create_error = "truncated basis file";
+            return RB_EFORMAT;
+        }
+        loads[r].field = fld;
+        loads[r].values = lvals[r].data();
+    }
+    prob.n_fields = hdr[11];
+    std::vector<double> fields((size_t)prob.n_fields * N);
+    if (prob.n_fields > 0) {
+        if (!take(fields.data(), fields.size() * sizeof(double))) {
+            g_create_error = "truncated basis file";
+            return RB_EFORMAT;
+        }
+        prob.fields = fields.data();
     }
     prob.loads = loads.data();
     std::string why;
     if (validate_problem(&prob, why) != RB_OK) { g_create_error = "basis file problem: " + why; return RB_EFORMAT; }
-    const long long N = (long long)prob.m[0] * prob.m[1] * prob.m[2];
-    const int Q = prob.nb[0] * prob.nb[1] * prob.nb[2];
+    const int Q = prob.n_fields > 0 ? prob.n_fields : prob.nb[0] * prob.nb[1] * prob.nb[2];
     const size_t need = ((size_t)N * n + (size_t)Q * n * n + (size_t)prob.n_loads * n + (size_t)n * n) * 8 +
                         (size_t)n * 4 + 8;
     if (buf.size() - off != need) { g_create_error = "basis file size does not match its header"; return RB_EFORMAT; }

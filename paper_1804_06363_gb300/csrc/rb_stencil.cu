@@ -526,7 +526,7 @@ __global__ void k_fill_loads(Geo g, int R, const int* kind, const double* center
     const int r = blockIdx.y;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
          i += (long long)gridDim.x * blockDim.x) {
-        double v = 1.0;
+        double v = kind[r] == RB_LOAD_CONST ? 1.0 : 0.0;   // array and boundary loads: copied by the host
         if (kind[r] == RB_LOAD_GAUSS) {
             int ix, iy, iz;
             node_xyz(g, i, ix, iy, iz);

@@ -25,13 +25,17 @@ GEMMS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
 STORES = {"f32": 0, "bf16": 1}
 
 
+LOAD_KINDS = {"const": 0, "gauss": 1, "array": 2, "boundary": 3}
+
+
 class RbLoad(C.Structure):
-    _fields_ = [("kind", C.c_int), ("param", C.c_int), ("center", C.c_double * 3), ("sigma", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("param", C.c_int), ("center", C.c_double * 3), ("sigma", C.c_double),
+                ("field", C.c_int), ("values", C.c_void_p)]
 
 
 class RbProblem(C.Structure):
     _fields_ = [("dim", C.c_int), ("m", C.c_int * 3), ("nb", C.c_int * 3), ("n_loads", C.c_int),
-                ("loads", C.POINTER(RbLoad)), ("n_mu", C.c_int)]
+                ("loads", C.POINTER(RbLoad)), ("n_mu", C.c_int), ("n_fields", C.c_int), ("fields", C.c_void_p)]
 
 
 class RbOpts(C.Structure):
@@ -159,16 +163,24 @@ def _f64(a) -> np.ndarray:
 
 
 def make_problem(prob):
-    """rb_problem from a problem description with dims, blocks, loads and n_mu."""
+    """rb_problem from a problem description with dims, blocks, loads and n_mu (and, for problems
+    with coefficient fields or array / boundary loads, field_values() and load_values(r)).
+    Returns the structure and the objects that must stay alive while it is used."""
     dims = list(prob.dims) + [1] * (3 - len(prob.dims))
     blocks = list(prob.blocks) + [1] * (3 - len(prob.blocks))
     loads = (RbLoad * len(prob.loads))()
+    keep = [loads]
     for i, ld in enumerate(prob.loads):
-        loads[i].kind = 0 if ld.kind == "const" else 1
+        loads[i].kind = LOAD_KINDS[ld.kind]
         loads[i].param = ld.param
         for j in range(3):
             loads[i].center[j] = ld.center[j]
         loads[i].sigma = ld.sigma
+        loads[i].field = getattr(ld, "field", 0)
+        if loads[i].kind >= 2:
+            vals = _f64(prob.load_values(i))
+            keep.append(vals)
+            loads[i].values = vals.ctypes.data
     p = RbProblem()
     p.dim = len(prob.dims)
     for j in range(3):
@@ -177,7 +189,13 @@ def make_problem(prob):
     p.n_loads = len(prob.loads)
     p.loads = C.cast(loads, C.POINTER(RbLoad))
     p.n_mu = prob.n_mu
-    return p, loads
+    fields = prob.field_values() if hasattr(prob, "field_values") else None
+    if fields is not None:
+        fields = _f64(fields)
+        keep.append(fields)
+        p.n_fields = fields.shape[0]
+        p.fields = fields.ctypes.data
+    return p, keep
 
 
 def make_opts(**kw) -> RbOpts:

@@ -53,7 +53,7 @@ def test_binding_covers_the_header(libpath):
 def test_struct_layouts_match_header(libpath):
     """Field order / sizes of the ctypes mirrors agree with the C structs."""
     from paper_1804_06363_gb300 import rb
-    assert ctypes.sizeof(rb.RbLoad) == 4 + 4 + 24 + 8
+    assert ctypes.sizeof(rb.RbLoad) == 4 + 4 + 24 + 8 + 4 + 4 + 8    # field, padding, values
     assert ctypes.sizeof(rb.RbStats) == 4 * 4 + 8 + 8       # n_used and the tail padding
     assert rb.RbStats.n_used.offset == 24
     assert rb.RbOpts.adaptive_n.offset == rb.RbOpts.store.offset + 4 and rb.RbOpts.gamma.offset % 8 == 0
@@ -71,6 +71,48 @@ def test_invalid_problem_is_rejected_without_gpu(libpath):
     st = rb.lib().rb_offline_load_arrays(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, 1)
     assert st == rb.RB_EINVAL and not h.value
     assert b"dim" in rb.lib().rb_last_error(None)
+
+
+def test_field_problems_are_validated_without_gpu(libpath):
+    """Coefficient fields and array / boundary loads: the checks of rb_problem run before any CUDA call."""
+    import workloads as wl
+    from paper_1804_06363_gb300 import rb
+    lib = rb.lib()
+    prob = wl.case_problem("case2", (6, 5, 4))
+    h = ctypes.c_void_p()
+
+    def rejected(edit, word):
+        p, keep = rb.make_problem(prob)
+        edit(p)
+        st = lib.rb_offline_load_arrays(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, 1)
+        assert st == rb.RB_EINVAL and not h.value
+        assert word in lib.rb_last_error(None), lib.rb_last_error(None)
+
+    def blocks(p):
+        p.nb[0] = 2
+    rejected(blocks, b"one block")
+
+    def field_index(p):
+        p.loads[1].field = 2
+    rejected(field_index, b"field index")
+
+    def no_values(p):
+        p.loads[0].values = None
+    rejected(no_values, b"values")
+
+    def no_fields(p):
+        p.fields = None
+    rejected(no_fields, b"n_fields")
+
+    def few_mu(p):
+        p.n_mu = 1
+    rejected(few_mu, b"n_mu")
+    # the no-allocation residual needs a context for such problems
+    p, keep = rb.make_problem(prob)
+    mu = (ctypes.c_double * 6)(1.0, 0.5, 0.5, 0.25, 0.5, 0.25)
+    out = (ctypes.c_double * 1)()
+    assert lib.rb_residual_noalloc(ctypes.byref(p), 1, mu, ctypes.c_void_p(16), out, None) == rb.RB_EINVAL
+    assert b"context" in lib.rb_last_error(None)
 
 
 def test_network_and_warm_start_arguments_are_validated_without_gpu(libpath):
@@ -120,8 +162,8 @@ def test_struct_layouts_match_compiled_header(tmp_path):
         pytest.skip("no C compiler")
     checks = {"rb_opts": (rb.RbOpts, ["tol", "nu", "omega", "inner_tol", "store", "adaptive_n", "gamma", "stream"]),
               "rb_stats": (rb.RbStats, ["iters", "status", "rel_res", "n_used"]),
-              "rb_problem": (rb.RbProblem, ["dim", "m", "nb", "n_loads", "loads", "n_mu"]),
-              "rb_load": (rb.RbLoad, ["kind", "param", "center", "sigma"]),
+              "rb_problem": (rb.RbProblem, ["dim", "m", "nb", "n_loads", "loads", "n_mu", "n_fields", "fields"]),
+              "rb_load": (rb.RbLoad, ["kind", "param", "center", "sigma", "field", "values"]),
               "rb_tune_result": (rb.RbTuneResult, ["nu", "inner_tol", "ms_per_solve", "store"]),
               "rb_kernel_time": (rb.RbKernelTime, ["name", "launches", "ms"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rb.h"', "int main(void) {"]

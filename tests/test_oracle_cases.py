@@ -1,0 +1,208 @@
+"""Pins of the oracle's coefficient-field operator and Dirichlet lift, the finite-difference
+analogues of the paper's Case 1 and Case 2 (Section 5, Table 1).
+
+What fixes the values here is the PDE, not the oracle: manufactured solutions of
+-div(kappa grad u) = f with the cases' coefficient, whose nodal error must fall by 4x when h
+halves (the scheme is second order), a discrete eigenvector in closed form, and the reduction
+of the field form to the block form already pinned against the incidence-form operator.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import direct, greedy
+from oracle import problem as pb
+from oracle import rb
+from tests import pins
+
+
+@dataclasses.dataclass(frozen=True)
+class _Given(wl.Problem):
+    """A problem whose fields and load arrays are given by functions of the node coordinates
+    (interior nodes; the grid with its boundary layer for boundary loads)."""
+    fields_fn: tuple = ()
+    load_fns: tuple = ()
+
+    def field_values(self):
+        c = wl._coords(self.dims, False)
+        return np.stack([np.broadcast_to(f(c), pb.grid_shape(self)).reshape(-1) for f in self.fields_fn])
+
+    def load_values(self, r):
+        ld = self.loads[r]
+        ext = ld.kind == "boundary"
+        c = wl._coords(self.dims, ext)
+        shape = tuple(s + 2 for s in pb.grid_shape(self)) if ext else pb.grid_shape(self)
+        return np.broadcast_to(self.load_fns[r](c), shape).reshape(-1).astype(np.float64)
+
+
+MU1 = 0.7   # the Case 1 parameter of the manufactured problems
+
+
+def _kappa_case1(c):
+    return 1.0 + MU1 * sum((x - 0.5) ** 2 for x in c)
+
+
+def _grad_kappa_case1(c, d):
+    return 2.0 * MU1 * (c[d] - 0.5)
+
+
+def _sines(c):
+    out = 1.0
+    for x in c:
+        out = out * np.sin(math.pi * x)
+    return out
+
+
+def _manufactured_zero_bc(dim):
+    """u = prod sin(pi x_d), kappa = 1 + mu r^2: f = kappa d pi^2 u - grad kappa . grad u."""
+    def u(c):
+        return _sines(c)
+
+    def f(c):
+        out = _kappa_case1(c) * dim * math.pi ** 2 * _sines(c)
+        for d in range(dim):
+            du = math.pi * np.cos(math.pi * c[d])
+            for e in range(dim):
+                if e != d:
+                    du = du * np.sin(math.pi * c[e])
+            out = out - _grad_kappa_case1(c, d) * du
+        return out
+    return u, f
+
+
+def _manufactured_dirichlet(dim):
+    """u = cos(pi x) exp(y) [cos(pi z / 2)], non-zero on the boundary."""
+    def u(c):
+        out = np.cos(math.pi * c[0]) * np.exp(c[1])
+        if dim == 3:
+            out = out * np.cos(0.5 * math.pi * c[2])
+        return out
+
+    def f(c):
+        lap = -math.pi ** 2 + 1.0 - (0.25 * math.pi ** 2 if dim == 3 else 0.0)
+        grads = [-math.pi * np.sin(math.pi * c[0]) * np.exp(c[1]), np.cos(math.pi * c[0]) * np.exp(c[1])]
+        if dim == 3:
+            z = np.cos(0.5 * math.pi * c[2])
+            grads = [grads[0] * z, grads[1] * z,
+                     -0.5 * math.pi * np.cos(math.pi * c[0]) * np.exp(c[1]) * np.sin(0.5 * math.pi * c[2])]
+        out = -_kappa_case1(c) * lap * u(c)
+        for d in range(dim):
+            out = out - _grad_kappa_case1(c, d) * grads[d]
+        return out
+    return u, f
+
+
+def _case1_fields():
+    return (lambda c: np.ones_like(sum(c)), lambda c: sum((x - 0.5) ** 2 for x in c))
+
+
+def _nodal_error(prob, mu, u):
+    x = direct.sparse_direct(prob, mu)
+    ue = np.broadcast_to(u(wl._coords(prob.dims, False)), pb.grid_shape(prob)).reshape(-1)
+    return np.abs(x - ue).max()
+
+
+@pytest.mark.parametrize("dim,sizes", [(2, (15, 31, 63)), (3, (7, 15, 31))])
+def test_field_operator_is_second_order_on_a_manufactured_solution(dim, sizes):
+    """Case 1 coefficient, zero boundary data: the error at the nodes falls by 4x per halving of h."""
+    u, f = _manufactured_zero_bc(dim)
+    errs = []
+    for m in sizes:
+        prob = _Given(dims=(m,) * dim, blocks=(1,) * dim, loads=(wl.Load("array"),), coefficient="case1",
+                      fields_fn=_case1_fields(), load_fns=(f,))
+        errs.append(_nodal_error(prob, np.array([1.0, MU1]), u))
+    for a, b in zip(errs, errs[1:]):
+        assert 3.6 < a / b < 4.4, errs
+
+
+@pytest.mark.parametrize("dim,sizes,lo", [(2, (31, 63, 127), 3.3), (3, (7, 15, 31), 2.8)])
+def test_dirichlet_lift_is_second_order_on_a_manufactured_solution(dim, sizes, lo):
+    """Non-zero boundary data lifted through kappa = F_0 + mu F_1 (one boundary load per field,
+    weights 1 and mu).  The face to the boundary carries kappa at the node, half a cell from the
+    face, an O(1) consistency error confined to the boundary rows; the global error is still
+    second order, approached from below (2D ratios 3.45, 3.69, 3.83 from m = 31 to 255; 3D
+    pre-asymptotic at these sizes, ratio 2.96 from 15 to 31).  A lift through the wrong field,
+    face, sign or boundary node does not converge at all."""
+    u, f = _manufactured_dirichlet(dim)
+    errs = []
+    for m in sizes:
+        loads = (wl.Load("array"), wl.Load("boundary", param=0, field=0), wl.Load("boundary", param=1, field=1))
+        prob = _Given(dims=(m,) * dim, blocks=(1,) * dim, loads=loads, coefficient="case1",
+                      fields_fn=_case1_fields(), load_fns=(f, u, u))
+        errs.append(_nodal_error(prob, np.array([1.0, MU1]), u))
+    ratios = [a / b for a, b in zip(errs, errs[1:])]
+    assert lo < ratios[-1] < 4.4 and ratios[-1] > ratios[0], errs
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_case1_at_mu_zero_has_the_closed_form_discrete_solution(dim):
+    """kappa = 1: prod sin(pi x_d) is an eigenvector of the FD Laplacian with eigenvalue
+    sum_d 4 sin^2(pi h / 2) / h^2, so u_h = d pi^2 / lambda prod sin(pi x_d)."""
+    m = 9
+    w = wl.paper_case("case1", m, dim=dim)
+    h = 1.0 / (m + 1)
+    lam = dim * 4.0 * math.sin(math.pi * h / 2) ** 2 / h ** 2
+    c = wl._coords(w.problem.dims, False)
+    expect = np.broadcast_to(dim * math.pi ** 2 / lam * _sines(c), pb.grid_shape(w.problem)).reshape(-1)
+    x = direct.sparse_direct(w.problem, wl.case_theta("case1", [0.0]))
+    np.testing.assert_allclose(x, expect, rtol=1e-12, atol=1e-13)
+
+
+def test_indicator_fields_reproduce_the_block_operator():
+    """Fields equal to the block indicators give the block problem's operator (itself pinned
+    against the incidence form), for every parameter vector."""
+    dims, blocks = (7, 5, 4), (2, 1, 2)
+    blk = wl.small(dims, blocks, n_basis=1).problem
+    ind = pb.node_block(blk)
+    fields = tuple((lambda c, q=q: (ind == q).astype(float)) for q in range(blk.P))
+
+    @dataclasses.dataclass(frozen=True)
+    class _Ind(_Given):
+        @property
+        def P(self):
+            return len(self.fields_fn)
+
+    prob = _Ind(dims=dims, blocks=(1, 1, 1), loads=(wl.Load("const"),), coefficient="case1", fields_fn=fields)
+    mu = np.exp(np.random.default_rng(3).uniform(-2.0, 2.0, blk.P))
+    A = pins.incidence_operator(dims, blocks, mu)
+    np.testing.assert_allclose(pb.assemble_csr(prob, mu).toarray(), A, rtol=1e-14, atol=1e-12)
+    v = np.random.default_rng(4).standard_normal(prob.n_dof)
+    np.testing.assert_allclose(pb.apply(prob, mu, v), A @ v, rtol=1e-13, atol=1e-12 * np.abs(A).max())
+
+
+def test_case2_load_is_the_lift_of_its_boundary_data():
+    """The four lift terms with weights (1 - mu_2), mu_1 (1 - mu_2), mu_2, mu_1 mu_2 add up to the
+    lift of g(mu) = (1 - mu_2) g_a + mu_2 g_b through kappa(mu) = 1 + mu_1 F_1: the affine split
+    of the load is exact."""
+    w = wl.paper_case("case2", 9, dim=3)
+    prob = w.problem
+    for m in w.draw_physical(11, 3):
+        theta = wl.case_theta("case2", m)
+        K = pb.node_coefficient(prob, theta)
+        ga = prob.load_values(1).reshape(tuple(s + 2 for s in pb.grid_shape(prob)))
+        gb = prob.load_values(3).reshape(ga.shape)
+        g = (1.0 - m[1]) * ga + m[1] * gb
+        expect = prob.load_values(0) + pb.boundary_lift(prob, K, g)
+        np.testing.assert_allclose(pb.load(prob, theta), expect, rtol=1e-13, atol=1e-10)
+        # kappa(mu) at the nodes is 1 + mu_1 sin^2(20 pi s(x))
+        c = wl._coords(prob.dims, False)
+        s = 4.0 * (c[0] - 0.5) ** 2 + (c[1] - 0.5) ** 2 + (c[2] - 0.5) ** 2
+        np.testing.assert_allclose(K, 1.0 + m[0] * np.sin(20.0 * math.pi * s) ** 2, rtol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["case1", "case2"])
+def test_rbcg_on_the_cases_reaches_the_truth_and_beats_cg(case):
+    """Alg. 3 on a small grid of each case with a greedy basis: the solution matches the sparse
+    direct truth, and RBCG needs far fewer steps than plain CG (the paper's qualitative result)."""
+    w = wl.paper_case(case, 12, dim=3, n_basis=6, n_train=40)
+    prob = w.problem
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    for mu in w.test_mu(3):
+        res = rb.rbcg(basis, mu, tol=1e-10, max_iter=500)
+        truth = direct.sparse_direct(prob, mu)
+        assert np.linalg.norm(res.x - truth) <= 1e-8 * np.linalg.norm(truth)
+        _, plain_iters, _ = direct.cg(prob, mu, tol=1e-10)
+        assert res.iters * 2 <= plain_iters, (res.iters, plain_iters)

@@ -13,6 +13,15 @@ The grid, block partition and load terms of each workload are plain data
 here; the discretisation itself is written independently in `oracle/` and in
 the CUDA kernels.
 
+The paper's two test cases (Section 5, Table 1) are finite-difference analogues
+of the same family with coefficient FIELDS instead of blocks:
+    kappa(x; mu) = sum_q theta_q F_q(x)   (F_q given at the nodes),
+    u = g(x; mu) on the boundary, lifted into load terms.
+For them this module evaluates the fields, the source and the boundary data at
+the nodes (input data, like the Gaussian bumps' parameters) and maps the
+physical parameters of the paper's domain to the affine coefficients theta_q,
+phi_r that both the oracle and the library take as the parameter vector.
+
 Random numbers come from SplitMix64 (Steele, Lea & Flood 2014, "Fast
 splittable pseudorandom number generators"): state += 0x9E3779B97F4A7C15,
 then two xor-shift-multiply rounds.  A double in [0, 1) is (z >> 11) * 2^-53.
@@ -54,27 +63,36 @@ def uniform01(seed: int, count: int) -> np.ndarray:
 class Load:
     """One load term f_r of f(mu) = sum_r phi_r(mu) f_r.
 
-    kind  : "const" (f_r = 1 at every node) or "gauss"
-            (f_r(x) = exp(-|x - center|^2 / (2 sigma^2)) at node coordinates).
+    kind  : "const" (f_r = 1 at every node), "gauss"
+            (f_r(x) = exp(-|x - center|^2 / (2 sigma^2)) at node coordinates),
+            "array" (f_r = the node values of the source `recipe`) or
+            "boundary" (the lift of the Dirichlet data `recipe` through the
+            coefficient field `field`: the boundary faces' terms F_field(i) g(j) / h^2
+            moved to the right-hand side).
     param : -1 means phi_r = 1; otherwise phi_r = mu[param].
     """
     kind: str
     param: int = -1
     center: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     sigma: float = 0.0
+    recipe: str = ""
+    field: int = 0
 
 
 @dataclasses.dataclass(frozen=True)
 class Problem:
     """Grid, block partition and load terms of one parametrized diffusion problem.
 
-    dims   : interior nodes per direction, (mx, my) or (mx, my, mz); x fastest.
-    blocks : blocks per direction; P = prod(blocks) diffusion parameters.
-    loads  : load terms; mu has P + n_load_params entries.
+    dims        : interior nodes per direction, (mx, my) or (mx, my, mz); x fastest.
+    blocks      : blocks per direction; P = prod(blocks) diffusion parameters.
+    loads       : load terms; mu has P + n_load_params entries.
+    coefficient : "blocks" (kappa = mu_p on block p) or the name of a field recipe
+                  (kappa = sum_q mu_q F_q(x), P = number of fields; blocks are all 1).
     """
     dims: Tuple[int, ...]
     blocks: Tuple[int, ...]
     loads: Tuple[Load, ...]
+    coefficient: str = "blocks"
 
     @property
     def dim(self) -> int:
@@ -86,7 +104,26 @@ class Problem:
 
     @property
     def P(self) -> int:
+        if self.coefficient != "blocks":
+            return len(FIELD_RECIPES[self.coefficient])
         return int(np.prod(self.blocks))
+
+    def field_values(self) -> np.ndarray | None:
+        """[P][N_dof] node values of the coefficient fields (None for block coefficients)."""
+        if self.coefficient == "blocks":
+            return None
+        return _field_values(self.dims, self.coefficient)
+
+    def load_values(self, r: int) -> np.ndarray | None:
+        """Values of an "array" load at the nodes [N_dof], or of a "boundary" load's Dirichlet
+        data on the grid extended by the boundary layer [(mz+2)][(my+2)][(mx+2)] (x fastest);
+        None for the other kinds."""
+        ld = self.loads[r]
+        if ld.kind == "array":
+            return _source_values(self.dims, ld.recipe)
+        if ld.kind == "boundary":
+            return _boundary_values(self.dims, ld.recipe)
+        return None
 
     @property
     def n_mu(self) -> int:
@@ -108,14 +145,27 @@ class Workload:
     train_seed: int = 1
     test_seed: int = 2
     bump_seed: int = 3
+    case: str = ""                         # "case1" / "case2": parameters drawn in the paper's domain
+
+    def draw_physical(self, seed: int, count: int) -> np.ndarray:
+        """count x d physical parameters of a paper case, uniform in its domain (Section 5:
+        [0, 1] for Case 1, [0, 2] x [0, 1] for Case 2)."""
+        dom = CASE_DOMAINS[self.case]
+        u = uniform01(seed, count * len(dom)).reshape(count, len(dom))
+        lo = np.array([a for a, _ in dom])
+        hi = np.array([b for _, b in dom])
+        return lo + u * (hi - lo)
 
     def draw_mu(self, seed: int, count: int) -> np.ndarray:
         """count x n_mu parameter vectors from stream `seed`.
 
         Each vector draws n_mu uniforms in order; the first P become
         exp(ln a + u (ln b - ln a)) (log-uniform block values), the rest
-        lo + u (hi - lo) (load parameters).
+        lo + u (hi - lo) (load parameters).  For a paper case the vectors are the
+        affine coefficients case_theta(physical parameters).
         """
+        if self.case:
+            return np.stack([case_theta(self.case, m) for m in self.draw_physical(seed, count)])
         P, n_mu = self.problem.P, self.problem.n_mu
         u = uniform01(seed, count * n_mu).reshape(count, n_mu)
         a, b = self.mu_range
@@ -198,22 +248,134 @@ def small(dims: Sequence[int], blocks: Sequence[int], n_basis: int, n_train: int
                     n_train=n_train, n_test=16, batch=16)
 
 
+# ---------------------------------------------------------------------------
+# The paper's test cases (Section 5, Table 1) on finite-difference grids.
+#
+#   Case 1: kappa = 1 + mu r^2, r^2 = sum_d (x_d - 1/2)^2, g = 0, mu in [0, 1]
+#           -> A(mu) = A_1 + mu A_2 (fields F_0 = 1, F_1 = r^2), theta = (1, mu).
+#   Case 2: kappa = 1 + mu_1 sin^2(20 pi s(x)), s = 4 (x - 1/2)^2 + sum_{d>0} (x_d - 1/2)^2,
+#           g = (1 - mu_2) cos(10 pi s(x)) + mu_2 cos(10 pi sum_d x_d), mu in [0, 2] x [0, 1]
+#           -> A(mu) = A_1 + mu_1 A_2, and the lift of g through kappa(mu) gives four load
+#           terms besides the source, with phi = (1 - mu_2), mu_1 (1 - mu_2), mu_2, mu_1 mu_2.
+#   Both: source f = d pi^2 prod_d sin(pi x_d) (the paper's 3 pi^2 sin sin sin in 3D; the
+#   sign is that of the SPD form -div(kappa grad u) = f).
+
+CASE_DOMAINS = {"case1": ((0.0, 1.0),), "case2": ((0.0, 2.0), (0.0, 1.0))}
+
+
+def _coords(dims, extended: bool):
+    """Node coordinates per direction (x first): interior nodes (i + 1) h, or the grid extended by
+    the boundary layer, e h for e = 0 .. m + 1; each array broadcastable to the grid shape."""
+    out = []
+    nd = len(dims)
+    for d, m in enumerate(dims):
+        shape = [1] * nd
+        shape[nd - 1 - d] = m + 2 if extended else m
+        e = np.arange(m + 2) if extended else np.arange(m) + 1.0
+        out.append((e / (m + 1.0)).reshape(shape))
+    return out
+
+
+def _s(c):
+    """4 (x - 1/2)^2 + sum over the other directions of (x_d - 1/2)^2."""
+    return 4.0 * (c[0] - 0.5) ** 2 + sum((cd - 0.5) ** 2 for cd in c[1:])
+
+
+def _product(factors):
+    out = 1.0
+    for f in factors:
+        out = out * f
+    return out
+
+
+def _r2(c):
+    return sum((cd - 0.5) ** 2 for cd in c)
+
+
+FIELD_RECIPES = {
+    "case1": (lambda c: np.ones_like(_r2(c)), _r2),
+    "case2": (lambda c: np.ones_like(_r2(c)), lambda c: np.sin(20.0 * math.pi * _s(c)) ** 2),
+}
+SOURCE_RECIPES = {
+    "sine": lambda c: len(c) * math.pi ** 2 * _product(np.sin(math.pi * cd) for cd in c),
+}
+BOUNDARY_RECIPES = {
+    "case2_a": lambda c: np.cos(10.0 * math.pi * _s(c)),
+    "case2_b": lambda c: np.cos(10.0 * math.pi * sum(c)),
+}
+
+
+def _grid(dims, v, extended: bool):
+    shape = tuple(reversed([m + 2 if extended else m for m in dims]))
+    return np.broadcast_to(v, shape).reshape(-1).astype(np.float64)
+
+
+def _field_values(dims, name):
+    c = _coords(dims, False)
+    return np.stack([_grid(dims, f(c), False) for f in FIELD_RECIPES[name]])
+
+
+def _source_values(dims, name):
+    return _grid(dims, SOURCE_RECIPES[name](_coords(dims, False)), False)
+
+
+def _boundary_values(dims, name):
+    return _grid(dims, BOUNDARY_RECIPES[name](_coords(dims, True)), True)
+
+
+def case_theta(case: str, m) -> np.ndarray:
+    """Affine coefficients (theta_q of A, then the load weights) of a case's physical parameters."""
+    if case == "case1":
+        return np.array([1.0, float(m[0])])
+    if case == "case2":
+        m1, m2 = float(m[0]), float(m[1])
+        return np.array([1.0, m1, 1.0 - m2, m1 * (1.0 - m2), m2, m1 * m2])
+    raise ValueError(case)
+
+
+def case_problem(case: str, dims: Sequence[int]) -> Problem:
+    dims = tuple(dims)
+    blocks = (1,) * len(dims)
+    src = Load("array", recipe="sine")
+    if case == "case1":
+        return Problem(dims=dims, blocks=blocks, loads=(src,), coefficient="case1")
+    if case == "case2":
+        lift = [Load("boundary", param=2 + 2 * j + q, recipe=g, field=q)
+                for j, g in enumerate(("case2_a", "case2_b")) for q in (0, 1)]
+        return Problem(dims=dims, blocks=blocks, loads=(src, *lift), coefficient="case2")
+    raise ValueError(case)
+
+
+def paper_case(case: str, m: int = 64, dim: int = 3, n_basis: int = 20, n_train: int = 200,
+               n_test: int = 100) -> Workload:
+    """The paper's Case 1 / Case 2 on an m^dim interior grid (100 test parameters, as in the
+    paper's convergence study)."""
+    prob = case_problem(case, (m,) * dim)
+    name = f"{case}_{dim}d_{m}_n{n_basis}"
+    return Workload(name, prob, n_basis=n_basis, mu_range=(1.0, 1.0), load_range=(0.0, 1.0),
+                    n_train=n_train, n_test=n_test, batch=n_test, case=case)
+
+
 WORKLOADS = {
     "rbi_2d_64": rbi_2d_64,
     "rbcg_2d_512": rbcg_2d_512,
     "batched_3d_128": batched_3d_128,
     "batched_3d_64": lambda: ragged_3d(64),
     "large_3d_256": large_3d_256,
+    "case1_3d_64": lambda: paper_case("case1", 64),
+    "case2_3d_64": lambda: paper_case("case2", 64),
+    "case1_3d_128": lambda: paper_case("case1", 128, n_test=256),
 }
 
 
 def load_arrays(problem: Problem):
     """Flatten the load descriptors to arrays (kind code, param, centre, sigma).
 
-    kind code: 0 = const, 1 = gauss.  This is a format conversion for the
+    kind code: 0 = const, 1 = gauss, 2 = array, 3 = boundary.  This is a format conversion for the
     C interface, not arithmetic of the method.
     """
-    kinds = np.array([0 if ld.kind == "const" else 1 for ld in problem.loads], dtype=np.int32)
+    kinds = np.array([{"const": 0, "gauss": 1, "array": 2, "boundary": 3}[ld.kind] for ld in problem.loads],
+                     dtype=np.int32)
     params = np.array([ld.param for ld in problem.loads], dtype=np.int32)
     centers = np.array([ld.center for ld in problem.loads], dtype=np.float64).reshape(-1, 3)
     sigmas = np.array([ld.sigma for ld in problem.loads], dtype=np.float64)
