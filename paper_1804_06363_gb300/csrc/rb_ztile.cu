@@ -58,13 +58,25 @@ using namespace stg;
 
 namespace {
 
+// FP32 consumer threads per CTA at most and copies in flight per CTA (build-time tunables)
+#ifndef RB_Z_THREADS32
+#define RB_Z_THREADS32 448
+#endif
+#ifndef RB_Z_FLIGHT_KB
+#define RB_Z_FLIGHT_KB 96
+#endif
 constexpr int ZRING_MIN = 4;    // stages (planes) in the ring: at least 4, ...
 constexpr int ZRING_MAX = 10;
-constexpr size_t ZFLIGHT = 96 * 1024;   // ... and enough for about this many bytes in flight per CTA
+constexpr size_t ZFLIGHT = (size_t)RB_Z_FLIGHT_KB * 1024;   // ... and about this many bytes in flight per CTA
 constexpr int ZMAX_MX = 256;    // row length limit of these kernels
 // consumer threads at most (FP32 / FP64), plus one producer warp: 15 (8) warps keep 4 (2)
 // warps per SM sub-partition, 128 (255) registers per thread
-template <typename T> constexpr int zmax_consumers() { return sizeof(T) == 4 ? 448 : 224; }
+template <typename T> constexpr int zmax_consumers() { return sizeof(T) == 4 ? RB_Z_THREADS32 : 224; }
+// two FP32 CTAs per SM when they fit in the register file (each then keeps half the shared memory)
+template <typename T> constexpr int zmin_blocks() { return sizeof(T) == 4 && RB_Z_THREADS32 <= 224 ? 2 : 1; }
+template <typename T> constexpr size_t zsmem_cap() {
+    return zmin_blocks<T>() == 2 ? 110u * 1024u : 200u * 1024u;
+}
 
 // Shape of a launch, fixed on the host per geometry and kernel kind.
 struct ZPlan {
@@ -133,7 +145,7 @@ ZPlan zplan(const Geo& g, bool smoother, bool last) {
     int ring = 2 + (int)((ZFLIGHT + sb - 1) / sb);
     ring = ring < ZRING_MIN ? ZRING_MIN : (ring > ZRING_MAX ? ZRING_MAX : ring);
     while (ring > ZRING_MIN && ZLEAD + (ring * z.stage_elems + z.rbuf_elems) * sizeof(T) + ring * sizeof(uint64_t) >
-                                   200u * 1024u)
+                                   zsmem_cap<T>())
         --ring;
     z.ring = ring;
     z.ring_elems = (size_t)ring * z.stage_elems;
@@ -270,7 +282,7 @@ __device__ __forceinline__ T xat(const T* row, int x, int mx) {
 // r -= alpha A p, ||r||^2.
 
 template <typename T, bool PART_A>
-__global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPlan z, const __grid_constant__ ZMaps maps) {
+__global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3z_cg(Params P, ZPlan z, const __grid_constant__ ZMaps maps) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
     __shared__ double red[32];
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_cg(Params P, ZPl
 // (A p)^T y accumulated and the preconditioner finalised).
 
 template <typename T, bool LAST>
-__global__ void __launch_bounds__(zmax_consumers<T>() + 32) k3z_smooth(Params P, ZPlan z, T* dst_base,
+__global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3z_smooth(Params P, ZPlan z, T* dst_base,
                                                                        const __grid_constant__ ZMaps maps) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
@@ -750,7 +762,7 @@ template <typename T>
 bool ztile_fits(const Geo& g) {
     for (int kind = 0; kind < 4; ++kind) {
         const ZPlan z = zplan<T>(g, kind < 2, (kind & 1) != 0);
-        if (z.bytes > 200u * 1024u || z.nthr > zmax_consumers<T>() || (long long)z.ntile_y > tiles_flat(g.n) ||
+        if (z.bytes > zsmem_cap<T>() || z.nthr > zmax_consumers<T>() || (long long)z.ntile_y > tiles_flat(g.n) ||
             z.a_rows > 256)
             return false;
     }
