@@ -431,6 +431,7 @@ def n_sweep(args, w, ctx, dev, stream):
     (the greedy's bases are nested).  Per N: mean, best and worst step counts and their mid-range
     (the paper's Fig. 5 plots the average of the best and the worst case), and the throughput of
     the mixed-precision RBCG on the same queries."""
+    import numpy as np
     import torch
     from paper_1804_06363_gb300 import rb
     prob = w.problem

@@ -125,9 +125,23 @@ __device__ __noinline__ void multi_producer(const Params& P, const float* __rest
     drain_ring(full, u, (unsigned)S::RING, P.wait_ns);
 }
 
+// The 512-point instantiations know their thread count (160) and the CTAs per SM their shared
+// memory allows (4 for a pass before the last, 3 for the last, which stages p as well): the
+// register cap follows (96 and 128 registers a thread).  Build-time tunables.
+#ifndef RB_MS_BLOCKS_MID
+#define RB_MS_BLOCKS_MID 4
+#endif
+#ifndef RB_MS_BLOCKS_LAST
+#define RB_MS_BLOCKS_LAST 3
+#endif
+template <int MX>
+constexpr int ms_threads() { return MX > 0 ? MX / 4 + 32 : MAX_MX / 4 + 32; }
+template <int MX, bool LAST>
+constexpr int ms_min_blocks() { return MX > 0 ? (LAST ? RB_MS_BLOCKS_LAST : RB_MS_BLOCKS_MID) : 1; }
+
 template <int NF, bool LAST, int MX>
-__global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, const float* __restrict__ src_base,
-                                                                   float* dst_base) {
+__global__ void __launch_bounds__(ms_threads<MX>(), ms_min_blocks<MX, LAST>()) k2_smooth_multi(
+    Params P, const float* __restrict__ src_base, float* dst_base) {
     using S = MsShape<NF, LAST>;
     constexpr int NH = S::NH, RING_N = S::RING, LAG = S::LAG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -221,6 +235,10 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
         // one step of the march; PAR = k & 1: every half-sweep updates columns PAR, PAR + 2
         // UNI: the rows k .. k-NH+1 share one key (uniform across the CTA), so every half-sweep
         // uses cf; otherwise each forms its own coefficients
+        // slot of the stage d steps back (d <= RING_N, both known at compile time after unrolling)
+        auto ring_back = [&](unsigned slot, int d) -> unsigned {
+            return slot >= (unsigned)d ? slot - (unsigned)d : slot + (unsigned)(RING_N - d);
+        };
         auto step = [&](auto par_tag, auto uni_tag, int k, int kkey) {
             constexpr int PAR = decltype(par_tag)::value;
             constexpr bool UNI = decltype(uni_tag)::value != 0;
@@ -228,7 +246,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
             constexpr int K0 = 1 - PAR, K1 = 3 - PAR;      // the other colour's columns
             if (ok && !mb_wait(full + cslot, cpar, P.err, P.wait_ns)) ok = false;
             const uint32_t o_cur = cslot * stage_b;
-            const uint32_t o_prev = ((cslot + RING_N - 1) % RING_N) * stage_b;
+            const uint32_t o_prev = ring_back(cslot, 1) * stage_b;
             if constexpr (UNI) {
                 if (kkey != ckey) {
                     tcoef<float>(g, mus, x0, min(max(k, 0), my - 1), cf);
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
                         tcoef<float>(g, mus, x0, r, own);
                         c = ms_pick<J0>(own);
                     }
-                    const uint32_t o_r = ((cslot + RING_N - (unsigned)h) % RING_N) * stage_b;   // stage of row r
+                    const uint32_t o_r = ring_back(cslot, h) * stage_b;   // stage of row r
                     const V4t<float> rb = ld4(o_r + rx0);
                     // H_{i-1}'s value across the thread edge of row r (written in the previous step)
                     const float zh = ld1(eoff(h - 1, r) + (uint32_t)((PAR == 0 ? t : t + 2) * 4));
@@ -317,14 +335,14 @@ __global__ void __launch_bounds__(MAX_MX / 4 + 32) k2_smooth_multi(Params P, con
                     out.v[K1] = hc[NH - 2][1];
                     stg4(dst + (unsigned)(r * mx + x0), out);
                     if constexpr (LAST) {
-                        const uint32_t o_r = ((cslot + RING_N - (unsigned)(NH - 1)) % RING_N) * stage_b;
+                        const uint32_t o_r = ring_back(cslot, NH - 1) * stage_b;
                         const V4t<float> rb = ld4(o_r + rx0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) ry += rb.v[j] * out.v[j];
                         if (need_ap) {
                             // direction rows r-1, r, r+1 from their stages
-                            const uint32_t o_m = ((cslot + RING_N - (unsigned)NH) % RING_N) * stage_b;
-                            const uint32_t o_p = ((cslot + RING_N - (unsigned)(NH - 2)) % RING_N) * stage_b;
+                            const uint32_t o_m = ring_back(cslot, NH) * stage_b;
+                            const uint32_t o_p = ring_back(cslot, NH - 2) * stage_b;
                             const V4t<float> pm = ld4(o_m + px0), pc = ld4(o_r + px0), pn = ld4(o_p + px0);
                             const float pl = ld1(o_r + px0 - 4), pr = ld1(o_r + px0 + 16);
                             TCoef<float> own;
