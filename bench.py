@@ -454,19 +454,23 @@ def n_sweep(args, w, ctx, dev, stream):
         _, st_rbi = c.solve(mu, x, max_iter=20000, stream=stream.cuda_stream)
         x.zero_()
         _, st_cg = c.pcg(mu, x, precision="fp64", beta="pr", max_iter=5000, stream=stream.cuda_stream)
-        x.zero_()
-        c.pcg(mu, x, precision="mixed", stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        x.zero_()
-        e0.record(stream)
-        _, st_mx = c.pcg(mu, x, precision="mixed", stream=stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        rows.append({"N": n, "rbi_steps": summary(st_rbi), "rbcg_steps": summary(st_cg),
-                     "rbcg_mixed": {"solves_per_s": round(B / (e0.elapsed_time(e1) / 1000.0), 1),
-                                    "mean_inner_iters": float(st_mx["iters"].mean()),
-                                    "converged": int(np.sum(st_mx["status"] == rb.RB_OK))}})
+        row = {"N": n, "rbi_steps": summary(st_rbi), "rbcg_steps": summary(st_cg)}
+        # mixed precision with each engine of the projections: TF32 tensor cores (auto) and FP32
+        for key, gemm in (("rbcg_mixed_tf32", "auto"), ("rbcg_mixed_fp32", "cuda_cores")):
+            x.zero_()
+            c.pcg(mu, x, precision="mixed", gemm=gemm, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            _, st_mx = c.pcg(mu, x, precision="mixed", gemm=gemm, stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[key] = {"solves_per_s": round(B / (e0.elapsed_time(e1) / 1000.0), 1),
+                        "mean_inner_iters": float(st_mx["iters"].mean()),
+                        "mean_outer": float(st_mx["outer"].mean()),
+                        "converged": int(np.sum(st_mx["status"] == rb.RB_OK))}
+        rows.append(row)
         progress(f"N = {n}: RBI {rows[-1]['rbi_steps']['mid_range']}, RBCG {rows[-1]['rbcg_steps']['mid_range']} "
                  f"(mid-range of best and worst steps)")
         c.close()

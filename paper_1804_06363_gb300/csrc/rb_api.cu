@@ -277,10 +277,7 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
         l.values = l.kind >= RB_LOAD_ARRAY ? ctx->load_vals[r].data() : nullptr;
         if (l.kind != RB_LOAD_BOUNDARY) l.field = 0;
     }
-    if (ctx->n_fields > 0) {
-        ctx->h_fields.assign(prob->fields, prob->fields + (size_t)ctx->n_fields * ctx->N);
-        ctx->force_generic = true;   // the staged and tiled kernels take block coefficients only
-    }
+    if (ctx->n_fields > 0) ctx->h_fields.assign(prob->fields, prob->fields + (size_t)ctx->n_fields * ctx->N);
     for (int r = 0; r < ctx->R; ++r) ctx->load_param[r] = prob->loads[r].param;
     ctx->n_cap = n_cap;
     ctx->nbp = std::max(16, pad_to(n_cap, 16));
@@ -335,6 +332,14 @@ rb_status ctx_init(rb_ctx* ctx, const rb_problem* prob, int n_cap, int max_batch
         g.nf = ctx->n_fields;
         g.kf64 = ctx->d_kf64;
         g.kf32 = ctx->d_kf32;
+        if (ctx->dim == 3) {   // per-query node coefficients for the 3D tile kernels
+            double* k64;
+            float* k32;
+            TRY(dalloc(ctx, &k64, (size_t)B * N));
+            TRY(dalloc(ctx, &k32, (size_t)B * N));
+            g.kap64 = k64;
+            g.kap32 = k32;
+        }
     }
 
     // load terms
@@ -526,6 +531,14 @@ struct Mode {
     bool mixed;
 };
 
+// Kernel families a context may use.  Problems with coefficient fields run the generic
+// kernels, except on 3D grids that the z-march tile kernels cover (those read kappa(mu)).
+bool rowmarch_ok(const rb_ctx* ctx) { return use_rowmarch(ctx->geo) && !ctx->force_generic && ctx->n_fields == 0; }
+bool zmarch_ok(const rb_ctx* ctx, bool fp64) {
+    return use_zmarch_smoother(ctx->geo) && !ctx->force_generic &&
+           (ctx->n_fields == 0 || (ctx->geo.kap64 && use_ztile(ctx->geo, fp64)));
+}
+
 Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bool use_tc) {
     Params P{};
     P.g = ctx->geo;
@@ -571,7 +584,7 @@ Params make_params(rb_ctx* ctx, int B, double* x64, const rb_opts& o, Mode m, bo
     P.mixed = m.mixed ? 1 : 0;
     // BF16 iterates only where the staged red-black smoother runs (the mixed path)
     P.ybf16 = (m.mixed && o.store == RB_STORE_BF16 && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0 &&
-               !ctx->force_generic && use_rowmarch(ctx->geo) && use_tma_smoother(ctx->geo))
+               rowmarch_ok(ctx) && use_tma_smoother(ctx->geo))
                   ? 1
                   : 0;
     P.adaptive = (!m.rbi && o.adaptive_n > 0 && ctx->n > 0) ? 1 : 0;
@@ -633,7 +646,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 // One step of the per-query state machine for every active query.
 void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
     cudaStream_t s = L.s;
-    const bool rm = use_rowmarch(ctx->geo) && !ctx->force_generic;
+    const bool rm = rowmarch_ok(ctx);
     if (m.rbi) {
         timed(ctx, KK_RBI_RES, s, [&] { launch_rbi_residual(P, L); });
         cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);
@@ -661,7 +674,7 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
     enqueue_prec(ctx, P, L, o, m, use_tc);
     cudaMemsetAsync(ctx->d_lcnt + L_PREC, 0, sizeof(int), s);
     const bool staged = rm && o.kernels != 2 && use_staged_cg(ctx->geo);
-    const bool z3 = use_zmarch_smoother(ctx->geo) && !ctx->force_generic && o.kernels == 0;
+    const bool z3 = zmarch_ok(ctx, !m.mixed) && o.kernels == 0;
     if (m.mixed) {
         timed(ctx, KK_CG_A, s, [&] {
             if (staged) launch2d_cg_a_staged<float>(P, L);
@@ -695,8 +708,9 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
 // The RBI preconditioner y = RBI(A, r, W, 1) for every query on the PREC list.
 void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& o, Mode m, bool use_tc) {
     cudaStream_t s = L.s;
-    const bool rm = use_rowmarch(ctx->geo) && !ctx->force_generic;
-    const bool zm = use_zmarch_smoother(ctx->geo) && !ctx->force_generic;
+    const bool rm = rowmarch_ok(ctx);
+    const bool zm = zmarch_ok(ctx, !m.mixed);
+    const bool blocks = ctx->n_fields == 0;   // the z-march kernels of kernels = 1 take blocks only
     if (m.mixed) {
         if (use_tc) {
             timed(ctx, KK_TC_PROJECT, s, [&] { tc_project(ctx->tc, P, L); });
@@ -708,7 +722,7 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
             timed(ctx, KK_PROLONG, s, [&] { launch_prolong<float>(P, L, false); });
         }
         timed(ctx, KK_SMOOTH, s, [&] {
-            if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic &&
+            if (o.smoother == RB_SMOOTH_RBGS && o.kernels == 1 && !ctx->force_generic && blocks &&
                 use_fused_smoother(ctx->geo, o.nu))
                 launch2d_smooth_fused(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS && (o.kernels == 3 || o.kernels == 4) && !P.ybf16 &&
@@ -718,7 +732,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
                 launch2d_smooth_tma<float>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<float>(P, L, o.nu);
             else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0) launch3d_smooth_staged<float>(P, L, o.nu);
-            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1) launch3d_smooth<float>(P, L, o.nu);
+            else if (zm && blocks && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1)
+                launch3d_smooth<float>(P, L, o.nu);
             else launch_smoother<float>(P, L, o.nu, false);
         });
     } else {
@@ -730,7 +745,8 @@ void enqueue_prec(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
                 launch2d_smooth_tma<double>(P, L, o.nu);
             else if (rm && o.smoother == RB_SMOOTH_RBGS) launch2d_smooth<double>(P, L, o.nu);
             else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 0) launch3d_smooth_staged<double>(P, L, o.nu);
-            else if (zm && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1) launch3d_smooth<double>(P, L, o.nu);
+            else if (zm && blocks && o.smoother == RB_SMOOTH_RBGS && o.kernels == 1)
+                launch3d_smooth<double>(P, L, o.nu);
             else launch_smoother<double>(P, L, o.nu, false);
         });
     }
@@ -850,6 +866,7 @@ rb_status wave_begin(Wave& w, const double* mu_host) {
     }
     w.P = make_params(ctx, B, w.x64, w.o, w.m, w.use_tc);
     w.L = Launch{ctx->grid, s};
+    launch_field_kappa(ctx->geo, B, ctx->n_mu, ctx->d_mu, s);
     launch_cholesky(w.P, s, ctx->d_ANq, ctx->P);
     CK(cudaGetLastError());
     w.exec = nullptr;
@@ -1250,6 +1267,7 @@ rb_status rb_precondition(rb_ctx* ctx, int B, const double* mu, const void* r, v
     CK(cudaMemsetAsync(ctx->d_ndone, 0, sizeof(int), s));
     Params P = make_params(ctx, B, ctx->d_x64, o, m, use_tc);
     Launch L{ctx->grid, s};
+    launch_field_kappa(ctx->geo, B, ctx->n_mu, ctx->d_mu, s);
     launch_cholesky(P, s, ctx->d_ANq, ctx->P);
     CK(cudaMemcpyAsync(P.r, r, (size_t)B * N * es, cudaMemcpyDefault, s));
     if (ctx->n == 0) CK(cudaMemsetAsync(P.ypro, 0, (size_t)B * N * es, s));
@@ -1292,7 +1310,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
     // sweep count, for each storage of the smoother's iterates that applies (BF16
     // makes a sweep cheaper and may move the best nu)
     const bool bf16_ok = opts->precision == RB_PREC_MIXED && opts->smoother == RB_SMOOTH_RBGS &&
-                         !ctx->force_generic && use_rowmarch(ctx->geo) && use_tma_smoother(ctx->geo);
+                         rowmarch_ok(ctx) && use_tma_smoother(ctx->geo);
     const rb_opts start = best;
     for (int store = RB_STORE_F32; store <= (bf16_ok ? RB_STORE_BF16 : RB_STORE_F32); ++store) {
         for (int nu = 1; nu <= 6; ++nu) {
@@ -1321,8 +1339,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             const double ms = trial(t);
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
-        if (best.smoother == RB_SMOOTH_RBGS && !ctx->force_generic && (use_rowmarch(ctx->geo) || use_zmarch_smoother(ctx->geo)) &&
-            !ctx->force_generic) {
+        if (best.smoother == RB_SMOOTH_RBGS && ctx->n_fields == 0 && (rowmarch_ok(ctx) || zmarch_ok(ctx, false))) {
             const rb_opts base = best;
             for (int kk = 0; kk <= 4; ++kk) {
                 if (kk == base.kernels || (kk == 1 && ctx->geo.dim == 2 && !use_fused_smoother(ctx->geo, base.nu)))

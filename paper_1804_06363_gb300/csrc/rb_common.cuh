@@ -42,6 +42,8 @@ struct Geo {
     int nf;                      // coefficient fields (0: block coefficients)
     const double* kf64;          // [nf][n] node values of the fields
     const float* kf32;           // the same in FP32
+    const double* kap64;         // [Bmax][n] kappa(mu) = sum_q mu_q F_q at the nodes of each query slot
+    const float* kap32;          // (3D field problems; filled when a wave starts)
 };
 
 // Per-query phase of the solver state machine.
@@ -458,6 +460,8 @@ bool mlp_ready(const rb_mlp* net);
 rb_status mlp_predict_device(rb_mlp* net, int B, const double* d_mu, int ld_mu, double* d_out, cudaStream_t s);
 
 int tiles_flat(long long n);
+// kappa(mu_b) = sum_q mu_b,q F_q at every node of the first B query slots (g.kap64 / g.kap32)
+void launch_field_kappa(const Geo& g, int B, int n_mu, const double* mu, cudaStream_t s);
 int tiles_box(const Geo& g);
 
 // Where a caller's buffer lives.  Device memory of another GPU is rejected by

@@ -543,6 +543,29 @@ __global__ void k_fill_loads(Geo g, int R, const int* kind, const double* center
     }
 }
 
+// kappa(mu) at the nodes of each query slot, in FP64 and rounded to FP32 (the 3D tile kernels
+// read the node values of their tile's neighbourhood from these instead of the fields)
+__global__ void k_field_kappa(Geo g, int n_mu, const double* __restrict__ mu) {
+    const int b = blockIdx.y;
+    const double* m = mu + (size_t)b * n_mu;
+    double* k64 = const_cast<double*>(g.kap64) + (size_t)b * g.n;
+    float* k32 = const_cast<float*>(g.kap32) + (size_t)b * g.n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double k = 0.0;
+        for (int q = 0; q < g.nf; ++q) k += m[q] * __ldg(g.kf64 + (size_t)q * g.n + i);
+        k64[i] = k;
+        k32[i] = (float)k;
+    }
+}
+
+void launch_field_kappa(const Geo& g, int B, int n_mu, const double* mu, cudaStream_t s) {
+    if (g.nf <= 0 || !g.kap64 || !g.kap32 || B <= 0) return;
+    long long blocks = (g.n + THREADS - 1) / THREADS;
+    if (blocks > 1024) blocks = 1024;
+    k_field_kappa<<<dim3((unsigned)blocks, (unsigned)B), THREADS, 0, s>>>(g, n_mu, mu);
+}
+
 void launch_fill_loads(const Geo& g, int R, const int* kind, const double* center, const double* sigma, double* fr,
                        cudaStream_t s) {
     long long blocks = (g.n + THREADS - 1) / THREADS;

@@ -534,6 +534,10 @@ bool use_zmarch_smoother(const Geo& g) { return g.dim == 3 && tiles3(g) <= tiles
 template <typename T>
 void launch3d_smooth_staged(const Params& P, const Launch& L, int nu) {
     if (use_ztile(P.g, sizeof(T) == 8) && launch3d_smooth_tile<T>(P, L, nu)) return;
+    if (P.g.nf > 0) {   // the kernels below take block coefficients only
+        launch_smoother<T>(P, L, nu, false);
+        return;
+    }
     static bool configured = false;
     const size_t sm = sizeof(SmoothSmem<T>);
     if (!configured) {
@@ -560,6 +564,10 @@ template void launch3d_smooth_staged<double>(const Params&, const Launch&, int);
 template <typename T>
 void launch3d_cg_a(const Params& P, const Launch& L) {
     if (use_ztile(P.g, sizeof(T) == 8) && launch3d_cg_tile<T>(P, L, true)) return;
+    if (P.g.nf > 0) {
+        launch_cg_a<T>(P, L);
+        return;
+    }
     static bool configured = false;
     if (!configured) {
         allow_smem(k3s_cg<T, true>, sizeof(CgSmem<T>));
@@ -570,6 +578,10 @@ void launch3d_cg_a(const Params& P, const Launch& L) {
 template <typename T>
 void launch3d_cg_b(const Params& P, const Launch& L) {
     if (use_ztile(P.g, sizeof(T) == 8) && launch3d_cg_tile<T>(P, L, false)) return;
+    if (P.g.nf > 0) {
+        launch_cg_b<T>(P, L);
+        return;
+    }
     static bool configured = false;
     if (!configured) {
         allow_smem(k3s_cg<T, false>, sizeof(CgSmem<T>));

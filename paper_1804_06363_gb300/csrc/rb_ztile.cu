@@ -220,6 +220,58 @@ __device__ __forceinline__ void zcoef(const Geo& g, const T* mus, int x0, int y,
     }
 }
 
+template <typename T>
+__device__ __forceinline__ V4t<T> ldg4(const T* p);
+template <>
+__device__ __forceinline__ V4t<float> ldg4<float>(const float* p) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    return V4t<float>{{a.x, a.y, a.z, a.w}};
+}
+template <>
+__device__ __forceinline__ V4t<double> ldg4<double>(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return V4t<double>{{a.x, a.y, b.x, b.y}};
+}
+
+template <typename T>
+__device__ __forceinline__ const T* query_kappa(const Geo& g, int q);
+template <>
+__device__ __forceinline__ const float* query_kappa<float>(const Geo& g, int q) { return g.kap32 + (size_t)q * g.n; }
+template <>
+__device__ __forceinline__ const double* query_kappa<double>(const Geo& g, int q) { return g.kap64 + (size_t)q * g.n; }
+
+// zcoef for coefficient fields: the same face rule on the node values kappa(mu) of the query
+// (kq), read around the thread's 4 points of row y, plane k (mostly L1 hits: neighbouring threads,
+// rows and planes read the same values)
+template <typename T>
+__device__ __forceinline__ void zcoef_field(const Geo& g, const T* __restrict__ kq, int x0, int y, int k,
+                                            ZCoef<T>& c) {
+    const int mx = g.mx;
+    const size_t plane = (size_t)mx * g.my;
+    const size_t rb = (size_t)k * plane + (size_t)y * mx + x0;
+    const bool left = x0 > 0, right = x0 + 4 < mx, up = y > 0, dn = y < g.my - 1, zb = k > 0, zf = k < g.mz - 1;
+    const V4t<T> m = ldg4(kq + rb);
+    const V4t<T> mu_ = up ? ldg4(kq + rb - mx) : m, md = dn ? ldg4(kq + rb + mx) : m;
+    const V4t<T> mb = zb ? ldg4(kq + rb - plane) : m, mf = zf ? ldg4(kq + rb + plane) : m;
+    const T ml = left ? __ldg(kq + rb - 1) : m.v[0], mr = right ? __ldg(kq + rb + 4) : m.v[3];
+    const T hx = (T)g.ihx2, hy = (T)g.ihy2, hz = (T)g.ihz2, half = T(0.5);
+    c.kx[0] = hx * (left ? half * (m.v[0] + ml) : m.v[0]);
+#pragma unroll
+    for (int j = 1; j < 4; ++j) c.kx[j] = hx * half * (m.v[j - 1] + m.v[j]);
+    c.kx[4] = hx * (right ? half * (m.v[3] + mr) : m.v[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const T mc = m.v[j];
+        c.kym[j] = hy * (up ? half * (mc + mu_.v[j]) : mc);
+        c.kyp[j] = hy * (dn ? half * (mc + md.v[j]) : mc);
+        c.kzm[j] = hz * (zb ? half * (mc + mb.v[j]) : mc);
+        c.kzp[j] = hz * (zf ? half * (mc + mf.v[j]) : mc);
+        T dg = c.kx[j] + c.kx[j + 1] + c.kym[j] + c.kyp[j];
+        dg += c.kzm[j] + c.kzp[j];
+        c.idiag[j] = T(1) / dg;
+    }
+}
+
 // key of the z-dependence of a row's coefficients: the blocks of planes k-1, k, k+1
 __device__ __forceinline__ int zkey(const Geo& g, int k) {
     if (k < 0 || k >= g.mz) return -1;
@@ -281,7 +333,7 @@ __device__ __forceinline__ T xat(const T* row, int x, int mx) {
 // CG body.  PART_A: p_new = y + beta p_old, p^T A p.  Part B: d += alpha p,
 // r -= alpha A p, ||r||^2.
 
-template <typename T, bool PART_A>
+template <typename T, bool PART_A, bool FIELD>
 __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3z_cg(Params P, ZPlan z, const __grid_constant__ ZMaps maps) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T mus[MAX_MU];
@@ -407,10 +459,14 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3
                     vc = vp;
                     vp = a;
                     if (k >= z0 && row_ok) {
-                        const int kk = zkey(g, k);
-                        if (kk != ckey) {
-                            zcoef<T>(g, mus, x0, y, k, c);
-                            ckey = kk;
+                        if constexpr (FIELD) {
+                            zcoef_field<T>(g, query_kappa<T>(g, q), x0, y, k, c);
+                        } else {
+                            const int kk = zkey(g, k);
+                            if (kk != ckey) {
+                                zcoef<T>(g, mus, x0, y, k, c);
+                                ckey = kk;
+                            }
                         }
                         // plane k neighbours from stage k-1: rows y-1, y+1 and the x edges of row y
                         const T* ra = sp + z.off_a + own;
@@ -481,7 +537,7 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3
 // Smoother: one red-black sweep from src to dst (LAST: dst = y, r^T y and
 // (A p)^T y accumulated and the preconditioner finalised).
 
-template <typename T, bool LAST>
+template <typename T, bool LAST, bool FIELD>
 __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3z_smooth(Params P, ZPlan z, T* dst_base,
                                                                        const __grid_constant__ ZMaps maps) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -615,10 +671,14 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3
                 // ---- red half-sweep of plane k+1 at columns J
                 T n0 = T(0), n1 = T(0);
                 if (in_y && kr >= 0 && kr < g.mz) {
-                    const int kk = zkey(g, kr);
-                    if (kk != key[1 - PZ]) {   // (k + 1) & 1 == 1 - PZ
-                        zcoef<T>(g, mus, x0, y, kr, cf[1 - PZ]);
-                        key[1 - PZ] = kk;
+                    if constexpr (FIELD) {
+                        zcoef_field<T>(g, query_kappa<T>(g, q), x0, y, kr, cf[1 - PZ]);
+                    } else {
+                        const int kk = zkey(g, kr);
+                        if (kk != key[1 - PZ]) {   // (k + 1) & 1 == 1 - PZ
+                            zcoef<T>(g, mus, x0, y, kr, cf[1 - PZ]);
+                            key[1 - PZ] = kk;
+                        }
                     }
                     const ZCoef<T>& c = cf[1 - PZ];
                     // source plane k+1 (stage k-1): rows y-1, y+1 and the own row with its x edges
@@ -779,6 +839,50 @@ bool use_ztile(const Geo& g, bool fp64) {
     return fp64 ? ztile_fits<double>(g) : ztile_fits<float>(g);
 }
 
+// FIELD: coefficient fields (kappa(mu) read per row and plane) instead of block coefficients
+template <typename T, bool FIELD>
+void cg_tile_launch(const Params& P, const Launch& L, const ZPlan& z, const ZMaps& maps, bool part_a) {
+    const int threads = z.nthr + 32;
+    static size_t conf[2] = {0, 0};
+    static int grid[2] = {0, 0};
+    const int i = part_a ? 0 : 1;
+    if (conf[i] != z.bytes) {
+        grid[i] = part_a ? zgrid(k3z_cg<T, true, FIELD>, threads, z.bytes)
+                         : zgrid(k3z_cg<T, false, FIELD>, threads, z.bytes);
+        conf[i] = z.bytes;
+    }
+    if (part_a) k3z_cg<T, true, FIELD><<<grid[i], threads, z.bytes, L.s>>>(P, z, maps);
+    else k3z_cg<T, false, FIELD><<<grid[i], threads, z.bytes, L.s>>>(P, z, maps);
+}
+
+template <typename T, bool FIELD>
+void smooth_tile_launch(const Params& P, const Launch& L, const ZPlan& zl, const ZPlan& zi, const ZMaps& m_ypro,
+                        const ZMaps& m_tmp, int nu) {
+    T* ypro = reinterpret_cast<T*>(P.ypro);
+    T* tmp = reinterpret_cast<T*>(P.tmp);
+    T* out = reinterpret_cast<T*>(P.y);
+    static size_t conf[2] = {0, 0};
+    static int grid[2] = {0, 0};
+    if (conf[0] != zl.bytes) {
+        grid[0] = zgrid(k3z_smooth<T, true, FIELD>, zl.nthr + 32, zl.bytes);
+        conf[0] = zl.bytes;
+    }
+    if (conf[1] != zi.bytes) {
+        grid[1] = zgrid(k3z_smooth<T, false, FIELD>, zi.nthr + 32, zi.bytes);
+        conf[1] = zi.bytes;
+    }
+    const int sweeps = nu < 1 ? 1 : nu;
+    const T* src = ypro;
+    for (int s = 1; s <= sweeps; ++s) {
+        const bool last = s == sweeps;
+        T* dst = last ? out : ((s & 1) ? tmp : ypro);
+        const ZMaps& m = src == ypro ? m_ypro : m_tmp;
+        if (last) k3z_smooth<T, true, FIELD><<<grid[0], zl.nthr + 32, zl.bytes, L.s>>>(P, zl, dst, m);
+        else k3z_smooth<T, false, FIELD><<<grid[1], zi.nthr + 32, zi.bytes, L.s>>>(P, zi, dst, m);
+        src = dst;
+    }
+}
+
 template <typename T>
 bool launch3d_cg_tile(const Params& P, const Launch& L, bool part_a) {
     const ZPlan z = zplan<T>(P.g, false, part_a);
@@ -794,16 +898,8 @@ bool launch3d_cg_tile(const Params& P, const Launch& L, bool part_a) {
              zencode<T>(&maps.c, d, g, P.mixed ? P.Bmax : P.B, z.c_rows);
     }
     if (!ok) return false;
-    const int threads = z.nthr + 32;
-    static size_t conf[2] = {0, 0};
-    static int grid[2] = {0, 0};
-    const int i = part_a ? 0 : 1;
-    if (conf[i] != z.bytes) {
-        grid[i] = part_a ? zgrid(k3z_cg<T, true>, threads, z.bytes) : zgrid(k3z_cg<T, false>, threads, z.bytes);
-        conf[i] = z.bytes;
-    }
-    if (part_a) k3z_cg<T, true><<<grid[i], threads, z.bytes, L.s>>>(P, z, maps);
-    else k3z_cg<T, false><<<grid[i], threads, z.bytes, L.s>>>(P, z, maps);
+    if (g.nf > 0) cg_tile_launch<T, true>(P, L, z, maps, part_a);
+    else cg_tile_launch<T, false>(P, L, z, maps, part_a);
     return true;
 }
 template bool launch3d_cg_tile<float>(const Params&, const Launch&, bool);
@@ -816,33 +912,14 @@ bool launch3d_smooth_tile(const Params& P, const Launch& L, int nu) {
     const ZPlan zl = zplan<T>(g, true, true), zi = zplan<T>(g, true, false);
     T* ypro = reinterpret_cast<T*>(P.ypro);
     T* tmp = reinterpret_cast<T*>(P.tmp);
-    T* out = reinterpret_cast<T*>(P.y);
     ZMaps m_ypro, m_tmp;
     if (!zencode<T>(&m_ypro.a, ypro, g, P.Bmax, zl.a_rows) || !zencode<T>(&m_ypro.b, P.r, g, P.Bmax, zl.b_rows) ||
         !zencode<T>(&m_ypro.c, P.p, g, 2LL * P.Bmax, zl.c_rows) || !zencode<T>(&m_tmp.a, tmp, g, P.Bmax, zl.a_rows))
         return false;
     m_tmp.b = m_ypro.b;
     m_tmp.c = m_ypro.c;
-    static size_t conf[2] = {0, 0};
-    static int grid[2] = {0, 0};
-    if (conf[0] != zl.bytes) {
-        grid[0] = zgrid(k3z_smooth<T, true>, zl.nthr + 32, zl.bytes);
-        conf[0] = zl.bytes;
-    }
-    if (conf[1] != zi.bytes) {
-        grid[1] = zgrid(k3z_smooth<T, false>, zi.nthr + 32, zi.bytes);
-        conf[1] = zi.bytes;
-    }
-    const int sweeps = nu < 1 ? 1 : nu;
-    const T* src = ypro;
-    for (int s = 1; s <= sweeps; ++s) {
-        const bool last = s == sweeps;
-        T* dst = last ? out : ((s & 1) ? tmp : ypro);
-        const ZMaps& m = src == ypro ? m_ypro : m_tmp;
-        if (last) k3z_smooth<T, true><<<grid[0], zl.nthr + 32, zl.bytes, L.s>>>(P, zl, dst, m);
-        else k3z_smooth<T, false><<<grid[1], zi.nthr + 32, zi.bytes, L.s>>>(P, zi, dst, m);
-        src = dst;
-    }
+    if (g.nf > 0) smooth_tile_launch<T, true>(P, L, zl, zi, m_ypro, m_tmp, nu);
+    else smooth_tile_launch<T, false>(P, L, zl, zi, m_ypro, m_tmp, nu);
     return true;
 }
 template bool launch3d_smooth_tile<float>(const Params&, const Launch&, int);

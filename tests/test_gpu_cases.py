@@ -122,3 +122,39 @@ def test_offline_build_and_file_round_trip_on_a_case():
     for b in range(3):
         assert _rel(x1[b], direct.sparse_direct(prob, mu[b])) < 1e-9
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["case1", "case2"])
+def test_tile_kernels_with_fields_match_generic_kernels(name):
+    """On 3D grids whose rows hold a multiple of 4 points the z-march tile kernels read kappa(mu)
+    at the nodes (kernels = 0); the generic kernels (kernels = 2) evaluate the fields themselves.
+    The preconditioner agrees to round-off in FP64 and to FP32 level in the mixed engine, and both
+    FP64 solves reach the truth in the same number of iterations (+-1)."""
+    prob = wl.case_problem(name, (24, 20, 18))
+    w = wl.Workload(name, prob, n_basis=4, mu_range=(1.0, 1.0), load_range=(0.0, 1.0), n_train=24,
+                    n_test=3, batch=3, case=name)
+    basis = greedy.greedy(prob, w.train_mu(), w.n_basis)
+    mu = w.test_mu(3)
+    ctx = rb.Context.from_arrays(prob, basis.W, basis.ANq, basis.fNr, max_batch=3)
+    r = np.random.default_rng(4).standard_normal((3, prob.n_dof))
+    for nu in (1, 2):
+        yt = ctx.precondition(mu, r, precision="fp64", nu=nu, kernels=0)
+        yg = ctx.precondition(mu, r, precision="fp64", nu=nu, kernels=2)
+        assert np.abs(yt - yg).max() <= 1e-12 * np.abs(yg).max()
+        yt = ctx.precondition(mu, r.astype(np.float32), precision="mixed", nu=nu, kernels=0, gemm="cuda_cores")
+        yg = ctx.precondition(mu, r.astype(np.float32), precision="mixed", nu=nu, kernels=2, gemm="cuda_cores")
+        assert np.abs(yt - yg).max() <= 1e-5 * np.abs(yg).max()
+    truth = [direct.sparse_direct(prob, m) for m in mu]
+    x = np.zeros((3, prob.n_dof))
+    _, st_t = ctx.pcg(mu, x, precision="fp64", kernels=0)
+    for b in range(3):
+        assert _rel(x[b], truth[b]) < 1e-9
+    x[:] = 0.0
+    _, st_g = ctx.pcg(mu, x, precision="fp64", kernels=2)
+    assert np.all(np.abs(st_t["iters"].astype(int) - st_g["iters"].astype(int)) <= 1)
+    x[:] = 0.0
+    status, _ = ctx.pcg(mu, x, precision="mixed", kernels=0)
+    assert status == rb.RB_OK
+    for b in range(3):
+        assert _rel(x[b], truth[b]) < 1e-9
+    ctx.close()
