@@ -229,7 +229,7 @@ def tune(ctx, w, x, opts, n_sample: int = TUNE_SAMPLE):
     tB = min(x.shape[0], n_sample)
     tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
     opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
-                store=tuned["store"])
+                store=tuned["store"], x0=tuned["x0"])
     tuned["sample"] = f"{tB} training parameters"
     return tuned
 

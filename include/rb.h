@@ -87,7 +87,7 @@ typedef struct {
 enum { RB_SMOOTH_NONE = 0, RB_SMOOTH_RBGS = 1, RB_SMOOTH_JACOBI = 2 };
 enum { RB_PREC_FP64 = 0, RB_PREC_MIXED = 1 };
 enum { RB_BETA_FR = 0, RB_BETA_PR = 1 };
-enum { RB_X0_ZERO = 0, RB_X0_GIVEN = 1 };
+enum { RB_X0_ZERO = 0, RB_X0_GIVEN = 1, RB_X0_RB = 2 };
 enum { RB_GEMM_AUTO = 0, RB_GEMM_CUDA_CORES = 1, RB_GEMM_TENSOR = 2 };
 enum { RB_STORE_F32 = 0, RB_STORE_BF16 = 1 };
 
@@ -100,7 +100,11 @@ typedef struct {
     int precision;      /* RB_PREC_FP64: all FP64; RB_PREC_MIXED: FP32 inner RBCG
                            with FP64 residual refinement (rb_pcg only) */
     int beta_form;      /* RB_BETA_FR (Alg. 3 as printed) or RB_BETA_PR */
-    int x0_mode;        /* RB_X0_ZERO or RB_X0_GIVEN (x holds the start on entry) */
+    int x0_mode;        /* RB_X0_ZERO; RB_X0_GIVEN (x holds the start on entry); RB_X0_RB: start
+                           from the RB approximation x_hat(mu) = W a_N(mu) of eq. 3 (Galerkin
+                           coefficients of eq. 2 by FP64 Cholesky, lifted with the FP64 basis) -
+                           the point the first step of Alg. 2 / Alg. 3 reaches; with a basis that
+                           resolves the solution it saves the mixed solver its FP32 cycles */
     double inner_tol;   /* mixed: relative residual reduction of each FP32 solve */
     int max_outer;      /* mixed: maximum FP64 refinement steps */
     int gemm;           /* RB_GEMM_*: engine for the batched W^T R and W E products */
@@ -269,8 +273,8 @@ rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double
  * sweep count nu (1..6; the paper leaves the smoother's iteration count open,
  * Section 3.1) for each storage of the preconditioner's intermediate vectors that
  * applies (rb_opts.store), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6;
- * mixed only), the smoother kernels (rb_opts.kernels) and the GEMM engine (mixed
- * only).  Only configurations under which every
+ * mixed only), the smoother kernels (rb_opts.kernels), the GEMM engine (mixed
+ * only) and the start (zero or the RB approximation).  Only configurations under which every
  * sample query converges are eligible.  Writes the fastest into *opts and
  * summarises it in *res (may be NULL). */
 typedef struct {
@@ -281,6 +285,7 @@ typedef struct {
     int trials;
     int kernels;
     int store;
+    int x0_mode;           /* RB_X0_ZERO or RB_X0_RB (tried when opts->x0_mode is not RB_X0_GIVEN) */
 } rb_tune_result;
 rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* opts, rb_tune_result* res);
 

@@ -757,7 +757,7 @@ rb_status validate_opts(rb_ctx* ctx, const rb_opts& o) {
         (o.smoother < 0 || o.smoother > 2) || (o.beta_form != RB_BETA_FR && o.beta_form != RB_BETA_PR) ||
         (o.kernels < 0 || o.kernels > 4) || (o.store != RB_STORE_F32 && o.store != RB_STORE_BF16) ||
         (o.precision != RB_PREC_FP64 && o.precision != RB_PREC_MIXED) || o.adaptive_n < 0 ||
-        !(o.gamma >= 0.0)) {
+        !(o.gamma >= 0.0) || o.x0_mode < RB_X0_ZERO || o.x0_mode > RB_X0_RB) {
         ctx->err = "invalid options";
         return RB_EINVAL;
     }
@@ -837,12 +837,24 @@ rb_status wave_begin(Wave& w, const double* mu_host) {
         }
     }
     CK(cudaMemcpyAsync(ctx->d_mu, mu_host, (size_t)B * ctx->n_mu * sizeof(double), cudaMemcpyHostToDevice, s));
+    // RB_X0_RB: x_0 = W a_N(mu) (eqs. 2-3) in FP64; a query whose A_N(mu) is not positive definite
+    // starts from it all the same and the solve's own Cholesky reports the breakdown
+    const bool rb_start = w.o.x0_mode == RB_X0_RB && !w.x_given && ctx->n > 0;
+    if (rb_start) {
+        LoadMap lm{};
+        for (int r = 0; r < ctx->R; ++r) lm.param[r] = ctx->load_param[r];
+        CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+        launch_galerkin(ctx->n, ctx->P, ctx->d_ANq, ctx->R, lm, ctx->d_fNr, ctx->n_mu, B, ctx->d_mu, ctx->d_e64,
+                        ctx->d_flag, s);
+        launch_lift64(N, ctx->n, ctx->d_W64c, B, ctx->d_e64, w.x64, ctx->grid, s);
+        CK(cudaGetLastError());
+    }
     for (int q = 0; q < B; ++q) {
         QState& st = ctx->h_st[q];
         std::memset(&st, 0, sizeof(QState));
         st.phase = PH_OUTER;
         st.start = 1;
-        st.xzero = w.x_given ? 0 : 1;
+        st.xzero = (w.x_given || rb_start) ? 0 : 1;
         st.n_used = first_n_used(ctx, w.o, w.m);
     }
     CK(cudaMemcpyAsync(ctx->d_st, ctx->h_st, (size_t)B * sizeof(QState), cudaMemcpyHostToDevice, s));
@@ -854,7 +866,7 @@ rb_status wave_begin(Wave& w, const double* mu_host) {
     CK(cudaMemcpyAsync(ctx->d_lidx + L_OUT * ctx->Bmax, li.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_ndone, 0, sizeof(int), s));
     CK(cudaMemsetAsync(ctx->d_tick, 0, (size_t)B * sizeof(unsigned), s));
-    if (!w.x_given) CK(cudaMemsetAsync(w.x64, 0, (size_t)B * N * sizeof(double), s));
+    if (!w.x_given && !rb_start) CK(cudaMemsetAsync(w.x64, 0, (size_t)B * N * sizeof(double), s));
     if (w.m.mixed) CK(cudaMemsetAsync(ctx->d_d32, 0, (size_t)B * N * sizeof(float), s));
     // the host stages above are freed when the call returns: let them land first
     CK(cudaStreamSynchronize(s));
@@ -1307,6 +1319,17 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
     };
     rb_opts best = *opts;
     double best_ms = trial(best);
+    // the start: zero or the RB approximation (a basis that resolves the solutions makes the RB
+    // start converge in a step or two; a rougher one can make it slower than zero)
+    const bool try_start = opts->x0_mode != RB_X0_GIVEN && ctx->n > 0;
+    auto other_start = [&]() {
+        if (!try_start) return;
+        rb_opts t = best;
+        t.x0_mode = best.x0_mode == RB_X0_RB ? RB_X0_ZERO : RB_X0_RB;
+        const double ms = trial(t);
+        if (ms < best_ms) { best_ms = ms; best = t; }
+    };
+    other_start();
     // sweep count, for each storage of the smoother's iterates that applies (BF16
     // makes a sweep cheaper and may move the best nu)
     const bool bf16_ok = opts->precision == RB_PREC_MIXED && opts->smoother == RB_SMOOTH_RBGS &&
@@ -1353,6 +1376,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
             }
         }
     }
+    other_start();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_ms >= 1e299) { ctx->err = "no candidate configuration converged on the sample"; return RB_ENOCONV; }
@@ -1365,6 +1389,7 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
         res->trials = trials;
         res->kernels = best.kernels;
         res->store = best.store;
+        res->x0_mode = best.x0_mode;
     }
     return RB_OK;
 }

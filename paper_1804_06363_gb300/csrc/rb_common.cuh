@@ -437,7 +437,9 @@ struct LoadMap {
 void launch_galerkin(int nb, int Q, const double* ANq, int R, const LoadMap& lm, const double* fNr, int n_mu, int B,
                      const double* mu, double* coef, int* bad, cudaStream_t s);   // A_N(mu) a = f_N(mu)
 void launch_lift(long long n, int nb, const float* W32c, int B, const double* coef, double* x, int grid,
-                 cudaStream_t s);                                                  // x_b = W c_b
+                 cudaStream_t s);
+void launch_lift64(long long n, int nb, const double* W64c, int B, const double* coef, double* x, int grid,
+                   cudaStream_t s);                                                  // x_b = W c_b
 int coef_splits(int B, int num_sms);
 void launch_coefficients(long long n, int nb, const float* W32c, int B, const double* X, double* coef,
                          double* scratch, int num_sms, cudaStream_t s);            // c_b = W^T x_b

@@ -562,13 +562,14 @@ void launch_galerkin(int nb, int Q, const double* ANq, int R, const LoadMap& lm,
     k_galerkin<<<B, 128, (size_t)(nb * nb + nb) * sizeof(double), s>>>(nb, Q, ANq, R, lm, fNr, n_mu, mu, coef, bad);
 }
 
-// x_b = W c_b for B queries (FP32 products and sums, written as FP64): one pass
-// over W per group of LQ queries, points coalesced.
+// x_b = W c_b for B queries (products and sums in the precision of the given copy of W,
+// written as FP64): one pass over W per group of LQ queries, points coalesced.
 constexpr int LQ = 16;
 
-__global__ void __launch_bounds__(THREADS) k_lift(long long n, int nb, const float* __restrict__ Wc, int B,
+template <typename TW>
+__global__ void __launch_bounds__(THREADS) k_lift(long long n, int nb, const TW* __restrict__ Wc, int B,
                                                   const double* __restrict__ coef, double* __restrict__ x) {
-    __shared__ float cs[LQ][MAX_N];
+    __shared__ TW cs[LQ][MAX_N];
     const int groups = (B + LQ - 1) / LQ;
     const long long chunks = (n + TILE - 1) / TILE;
     for (long long w = blockIdx.x; w < (long long)groups * chunks; w += gridDim.x) {
@@ -577,20 +578,20 @@ __global__ void __launch_bounds__(THREADS) k_lift(long long n, int nb, const flo
         __syncthreads();
         for (int idx = threadIdx.x; idx < LQ * nb; idx += THREADS) {
             const int g = idx / nb, k = idx % nb, b = grp * LQ + g;
-            cs[g][k] = b < B ? (float)coef[(size_t)b * nb + k] : 0.0f;
+            cs[g][k] = b < B ? (TW)coef[(size_t)b * nb + k] : TW(0);
         }
         __syncthreads();
 #pragma unroll 1
         for (int j = 0; j < TILE / THREADS; ++j) {
             const long long i = ch * TILE + (long long)j * THREADS + threadIdx.x;
             if (i >= n) continue;
-            float acc[LQ];
+            TW acc[LQ];
 #pragma unroll
-            for (int g = 0; g < LQ; ++g) acc[g] = 0.0f;
+            for (int g = 0; g < LQ; ++g) acc[g] = TW(0);
             for (int k = 0; k < nb; ++k) {
-                const float wv = Wc[(size_t)k * n + i];
+                const TW wv = Wc[(size_t)k * n + i];
 #pragma unroll
-                for (int g = 0; g < LQ; ++g) acc[g] = fmaf(cs[g][k], wv, acc[g]);
+                for (int g = 0; g < LQ; ++g) acc[g] = fma(cs[g][k], wv, acc[g]);
             }
 #pragma unroll
             for (int g = 0; g < LQ; ++g) {
@@ -608,7 +609,18 @@ void launch_lift(long long n, int nb, const float* W32c, int B, const double* co
         cudaMemsetAsync(x, 0, (size_t)B * n * sizeof(double), s);
         return;
     }
-    k_lift<<<grid, THREADS, 0, s>>>(n, nb, W32c, B, coef, x);
+    k_lift<float><<<grid, THREADS, 0, s>>>(n, nb, W32c, B, coef, x);
+}
+
+// the same with the FP64 basis (products and sums in FP64): the RB approximation as a start
+void launch_lift64(long long n, int nb, const double* W64c, int B, const double* coef, double* x, int grid,
+                   cudaStream_t s) {
+    if (B == 0) return;
+    if (nb == 0) {
+        cudaMemsetAsync(x, 0, (size_t)B * n * sizeof(double), s);
+        return;
+    }
+    k_lift<double><<<grid, THREADS, 0, s>>>(n, nb, W64c, B, coef, x);
 }
 
 // part[sp][b][k] = sum over split sp of W[i][k] x_b[i]: FP32 products summed in

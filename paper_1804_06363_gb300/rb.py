@@ -23,6 +23,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 BETAS = {"fr": 0, "pr": 1}
 GEMMS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
 STORES = {"f32": 0, "bf16": 1}
+STARTS = {"zero": 0, "given": 1, "rb": 2}
 
 
 LOAD_KINDS = {"const": 0, "gauss": 1, "array": 2, "boundary": 3}
@@ -58,7 +59,7 @@ class RbBuildOpts(C.Structure):
 
 class RbTuneResult(C.Structure):
     _fields_ = [("nu", C.c_int), ("inner_tol", C.c_double), ("gemm", C.c_int), ("ms_per_solve", C.c_double),
-                ("trials", C.c_int), ("kernels", C.c_int), ("store", C.c_int)]
+                ("trials", C.c_int), ("kernels", C.c_int), ("store", C.c_int), ("x0_mode", C.c_int)]
 
 
 class RbKernelTime(C.Structure):
@@ -214,8 +215,8 @@ def make_opts(**kw) -> RbOpts:
             v = GEMMS[v] if isinstance(v, str) else v
         elif k == "store":
             v = STORES[v] if isinstance(v, str) else v
-        elif k == "x0":
-            k, v = "x0_mode", 1 if v else 0
+        elif k == "x0":   # "zero", "given", "rb", or a bool (True: given)
+            k, v = "x0_mode", STARTS[v] if isinstance(v, str) else (1 if v else 0)
         elif k == "stream":
             v = C.c_void_p(int(v) if v else 0)
         elif k == "graph":
@@ -506,7 +507,8 @@ class Context:
         inv = {v: k for k, v in GEMMS.items()}
         return {"nu": r.nu, "inner_tol": r.inner_tol, "gemm": inv.get(r.gemm, r.gemm),
                 "ms_per_solve": r.ms_per_solve, "trials": r.trials, "kernels": r.kernels,
-                "store": {v: k for k, v in STORES.items()}.get(r.store, r.store)}
+                "store": {v: k for k, v in STORES.items()}.get(r.store, r.store),
+                "x0": {v: k for k, v in STARTS.items()}.get(r.x0_mode, r.x0_mode)}
 
     def warm_start(self, mu, x, net: Optional[Mlp] = None, coef=None, stream: Optional[int] = None) -> int:
         """rb_warm_start: x [B][N_dof] (host or device) = W c(mu), c = Galerkin coefficients (net None)

@@ -164,7 +164,7 @@ def test_struct_layouts_match_compiled_header(tmp_path):
               "rb_stats": (rb.RbStats, ["iters", "status", "rel_res", "n_used"]),
               "rb_problem": (rb.RbProblem, ["dim", "m", "nb", "n_loads", "loads", "n_mu", "n_fields", "fields"]),
               "rb_load": (rb.RbLoad, ["kind", "param", "center", "sigma", "field", "values"]),
-              "rb_tune_result": (rb.RbTuneResult, ["nu", "inner_tol", "ms_per_solve", "store"]),
+              "rb_tune_result": (rb.RbTuneResult, ["nu", "inner_tol", "ms_per_solve", "store", "x0_mode"]),
               "rb_kernel_time": (rb.RbKernelTime, ["name", "launches", "ms"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rb.h"', "int main(void) {"]
     for cname, (_, fields) in checks.items():

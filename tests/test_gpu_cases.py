@@ -158,3 +158,26 @@ def test_tile_kernels_with_fields_match_generic_kernels(name):
     for b in range(3):
         assert _rel(x[b], truth[b]) < 1e-9
     ctx.close()
+
+
+def test_rb_approximation_start(case):
+    """rb_opts.x0_mode = RB_X0_RB starts from x_hat(mu) = W a_N(mu) (eqs. 2-3, FP64).  With a
+    tolerance the start already meets the solve returns it untouched: it equals the oracle's RB
+    approximation to round-off.  From it both solvers reach the truth."""
+    w, basis, mu, truth, ctx = case
+    n = w.problem.n_dof
+    x = torch.zeros((len(mu), n), dtype=torch.float64, device="cuda")
+    status, st = ctx.pcg(mu, x, precision="fp64", x0="rb", tol=1.0)
+    assert status == rb.RB_OK and np.all(st["iters"] == 0)
+    xs = x.cpu().numpy()
+    for b in range(len(mu)):
+        ref = orb.rb_approximation(basis, mu[b])
+        assert _rel(xs[b], ref) < 1e-12
+    status, _ = ctx.pcg(mu, x, precision="fp64", beta="pr", max_iter=1500, x0="rb")
+    assert status == rb.RB_OK
+    for b in range(len(mu)):
+        assert _rel(x[b].cpu().numpy(), truth[b]) < 1e-9
+    status, _ = ctx.pcg(mu, x, precision="mixed", x0="rb")
+    assert status == rb.RB_OK
+    for b in range(len(mu)):
+        assert _rel(x[b].cpu().numpy(), truth[b]) < 1e-9
