@@ -455,15 +455,17 @@ def n_sweep(args, w, ctx, dev, stream):
         x.zero_()
         _, st_cg = c.pcg(mu, x, precision="fp64", beta="pr", max_iter=5000, stream=stream.cuda_stream)
         row = {"N": n, "rbi_steps": summary(st_rbi), "rbcg_steps": summary(st_cg)}
-        # mixed precision with each engine of the projections: TF32 tensor cores (auto) and FP32
-        for key, gemm in (("rbcg_mixed_tf32", "auto"), ("rbcg_mixed_fp32", "cuda_cores")):
+        # mixed precision with each engine of the projections, TF32 tensor cores (auto) and FP32
+        # (zero start), and the FP32 engine from the RB approximation
+        for key, gemm, x0 in (("rbcg_mixed_tf32", "auto", "zero"), ("rbcg_mixed_fp32", "cuda_cores", "zero"),
+                              ("rbcg_mixed_fp32_rb_start", "cuda_cores", "rb")):
             x.zero_()
-            c.pcg(mu, x, precision="mixed", gemm=gemm, stream=stream.cuda_stream)
+            c.pcg(mu, x, precision="mixed", gemm=gemm, x0=x0, stream=stream.cuda_stream)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             x.zero_()
             e0.record(stream)
-            _, st_mx = c.pcg(mu, x, precision="mixed", gemm=gemm, stream=stream.cuda_stream)
+            _, st_mx = c.pcg(mu, x, precision="mixed", gemm=gemm, x0=x0, stream=stream.cuda_stream)
             e1.record(stream)
             torch.cuda.synchronize()
             row[key] = {"solves_per_s": round(B / (e0.elapsed_time(e1) / 1000.0), 1),
