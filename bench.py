@@ -67,7 +67,8 @@ BF16_SMOOTH_LAST, BF16_SMOOTH_SWEEP, BF16_PROLONG = 14, 8, 2
 
 # DRAM bytes per point and query of the dominant kernel from an ncu capture, valid only while the
 # kernel's source files hash to what they were when the counters were taken (otherwise the line
-# reports traffic null).  Filled from a capture of the current kernels.
+# reports traffic null).  Key: (inner precision, storage, kernel family, kernel, nu).  Filled from a
+# capture of the current kernels.
 NCU_TRAFFIC = {}
 
 
@@ -735,7 +736,7 @@ def main():
     achieved = kernels[dom].get("gbs")
     n_launch = max(1, kernels[dom]["launches"])
     traffic, traffic_src = None, None
-    nt = NCU_TRAFFIC.get((prec, opts.get("store", "f32"), dom, opts["nu"]))
+    nt = NCU_TRAFFIC.get((prec, opts.get("store", "f32"), opts.get("kernels", 0), dom, opts["nu"]))
     if nt is not None and source_hash(nt["sources"]) == nt["sha"]:
         traffic = round(nt["bytes_per_point"] * N * units[dom] / n_launch)
         traffic_src = nt["capture"]
