@@ -1374,6 +1374,17 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
                 const double ms = trial(t);
                 if (ms < best_ms) { best_ms = ms; best = t; }
             }
+            // a smoother that makes several sweeps per pass moves the best sweep count up
+            if (best.kernels >= 3) {
+                const rb_opts b2 = best;
+                for (int nu = 2; nu <= 9; ++nu) {
+                    if (nu == b2.nu) continue;
+                    rb_opts t = b2;
+                    t.nu = nu;
+                    const double ms = trial(t);
+                    if (ms < best_ms) { best_ms = ms; best = t; }
+                }
+            }
         }
     }
     other_start();
