@@ -270,8 +270,8 @@ rb_status rb_apply(rb_ctx* ctx, int B, const double* mu, const double* x, double
 
 /* Autotuner.  Times rb_pcg on the B sample queries (host mu; x host or device
  * [B][N_dof] scratch) and picks, by coordinate descent from *opts, the smoother
- * sweep count nu (1..6; the paper leaves the smoother's iteration count open,
- * Section 3.1) for each storage of the preconditioner's intermediate vectors that
+ * sweep count nu (1..6, then 2..9 once a smoother with several sweeps per pass is
+ * chosen; the paper leaves the smoother's iteration count open, Section 3.1) for each storage of the preconditioner's intermediate vectors that
  * applies (rb_opts.store), the FP32 cycle reduction inner_tol (1e-4, 1e-5, 1e-6;
  * mixed only), the smoother kernels (rb_opts.kernels), the GEMM engine (mixed
  * only) and the start (zero or the RB approximation).  Only configurations under which every
