@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RB-PCG solves/sec to rel. residual 1e-10 (mixed+batched vs FP64 plain), % HBM roofline"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rbcg_2d_512_oracle.json")
-TUNE_SAMPLE = 256          # training parameters the autotuner times (never the timed test queries)
+TUNE_SAMPLE = 256          # parameters the autotuner times (own seeded stream: not training, not test)
 PARITY_SEED = 7
 
 # Algorithmic bytes per grid point per launch unit (one query, one application), by kernel and
@@ -225,13 +225,14 @@ def base_options(precision: str, stream) -> dict:
 
 
 def tune(ctx, w, x, opts, n_sample: int = TUNE_SAMPLE):
-    """The autotuner on the workload's first n_sample training parameters (never the timed test
-    queries); updates opts with its choice and returns the summary."""
+    """The autotuner on n_sample parameters of its own seeded stream (neither the greedy's training
+    set nor the timed test queries); updates opts with its choice and returns the summary."""
+    import workloads as wl
     tB = min(x.shape[0], n_sample)
-    tuned = ctx.autotune(w.train_mu()[:tB], x[:tB], **opts)
+    tuned = ctx.autotune(wl.tune_mu(w, tB), x[:tB], **opts)
     opts.update(nu=tuned["nu"], inner_tol=tuned["inner_tol"], gemm=tuned["gemm"], kernels=tuned["kernels"],
                 store=tuned["store"], x0=tuned["x0"])
-    tuned["sample"] = f"{tB} training parameters"
+    tuned["sample"] = f"{tB} tuning parameters (seeded stream {wl.TUNE_SEED})"
     return tuned
 
 
@@ -485,7 +486,7 @@ def n_sweep(args, w, ctx, dev, stream):
 def leg_3d(args, dev, stream, peak, peak_kind):
     """The 3D workload (128^3, P = 8, n = 60, 256 queries per step) on the same GPU after the 2D
     results: basis built by the GPU greedy (snapshots by mixed-precision RBCG to 1e-11), the
-    autotuner on 64 training parameters, warm-up, timed steps with their own clock record, then a
+    autotuner on 64 tuning parameters, warm-up, timed steps with their own clock record, then a
     per-kernel pass for the roofline of its dominant kernel."""
     import numpy as np
     import torch
@@ -662,7 +663,7 @@ def main():
     opts = base_options(args.precision, stream.cuda_stream)
     opts.update(nu=args.nu, gemm=args.gemm, kernels=args.kernels)
 
-    # ---- autotuner (setup, not timed): on training parameters, never on the timed test queries
+    # ---- autotuner (setup, not timed): on its own parameter stream, never on the timed test queries
     tuned = None
     if not args.no_tune:
         tuned = tune(ctx, w, x, opts)

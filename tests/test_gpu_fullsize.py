@@ -4,7 +4,7 @@
   parameters as the oracle's greedy (tests/golden/rbcg_2d_512_oracle.json);
 * FP64 RBCG on the GPU takes the oracle's iteration counts on 16 test parameters;
 * the mixed-precision batch of 1000 queries, with the options bench.py times
-  (chosen by the same autotuner call on the same 256 training parameters),
+  (chosen by the same autotuner call on the same 256 tuning parameters),
   converges everywhere, and 32 seeded solutions match the oracle's sparse-direct
   truth to relative L2 1e-9 with an oracle-recomputed residual below 1e-10.
 """

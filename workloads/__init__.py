@@ -389,6 +389,14 @@ def load_arrays(problem: Problem):
 
 MLP_INIT_SEED = 4
 MLP_TRAIN_SEED = 5
+TUNE_SEED = 6       # the autotuner's sample: neither the greedy's training set nor the test queries
+
+
+def tune_mu(w: "Workload", count: int) -> np.ndarray:
+    """Parameter vectors the autotuner times (the workload's distribution, own stream).  Training
+    parameters would bias it: the greedy's snapshots are exact in the basis, so a start from the RB
+    approximation converges at once for them."""
+    return w.draw_mu(TUNE_SEED, count)
 
 
 def mlp_layer_sizes(n_in: int, n_out: int, hidden: int = 128) -> Tuple[int, ...]:
