@@ -658,16 +658,17 @@ void enqueue_step(rb_ctx* ctx, const Params& P, const Launch& L, const rb_opts& 
         return;
     }
     const bool staged_outer = rm && o.kernels != 2 && use_staged_outer(ctx->geo);
+    const bool tile_outer = !ctx->force_generic && o.kernels == 0 && use_ztile_outer(ctx->geo);
     if (m.mixed) {
         timed(ctx, KK_OUTER_UPDATE, s, [&] { launch_outer_update(P, L); });
         timed(ctx, KK_OUTER_RES, s, [&] {
             if (staged_outer) launch2d_outer_residual_staged<float>(P, L);
-            else launch_outer_residual<float>(P, L);
+            else if (!(tile_outer && launch3d_outer_tile<float>(P, L))) launch_outer_residual<float>(P, L);
         });
     } else {
         timed(ctx, KK_OUTER_RES, s, [&] {
             if (staged_outer) launch2d_outer_residual_staged<double>(P, L);
-            else launch_outer_residual<double>(P, L);
+            else if (!(tile_outer && launch3d_outer_tile<double>(P, L))) launch_outer_residual<double>(P, L);
         });
     }
     cudaMemsetAsync(ctx->d_lcnt + L_OUT, 0, sizeof(int), s);

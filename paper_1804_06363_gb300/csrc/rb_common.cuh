@@ -410,6 +410,10 @@ template <typename T> void launch3d_cg_b(const Params& P, const Launch& L);
 // 3D kernels marching in z over tiles of whole x-rows (rows of a multiple of 4 points, at most
 // 256): 4 points per thread, planes staged by bulk row copies, one CTA barrier per plane
 bool use_ztile(const Geo& g, bool fp64);
+// the FP64 outer residual on the same tiles (x staged with its halo rows)
+bool use_ztile_outer(const Geo& g);
+template <typename TR>
+bool launch3d_outer_tile(const Params& P, const Launch& L);
 // (false: a tensor map could not be encoded; nothing was launched)
 template <typename T> bool launch3d_cg_tile(const Params& P, const Launch& L, bool part_a);
 template <typename T> bool launch3d_smooth_tile(const Params& P, const Launch& L, int nu);

@@ -101,8 +101,9 @@ size_t zalign(size_t elems) {   // round up to a multiple of 128 bytes
     return (elems + q - 1) / q * q;
 }
 
+// outer = true: the FP64 outer residual (only x with its halo rows is staged)
 template <typename T>
-ZPlan zplan(const Geo& g, bool smoother, bool last) {
+ZPlan zplan(const Geo& g, bool smoother, bool last, bool outer = false) {
     ZPlan z{};
     const int tx = g.mx / 4;
     z.txp = tx <= 16 ? 16 : ((tx + 31) / 32) * 32;
@@ -128,6 +129,10 @@ ZPlan zplan(const Geo& g, bool smoother, bool last) {
     } else if (last) {         // part A: a: y, b: p_old
         z.a_rows = z.ty + 2;
         z.b_rows = z.ty + 2;
+        z.c_rows = 0;
+    } else if (outer) {        // outer residual: a: x
+        z.a_rows = z.ty + 2;
+        z.b_rows = 0;
         z.c_rows = 0;
     } else {                   // part B: a: p, b: r, c: d
         z.a_rows = z.ty + 2;
@@ -534,6 +539,164 @@ __global__ void __launch_bounds__(zmax_consumers<T>() + 32, zmin_blocks<T>()) k3
 }
 
 // ---------------------------------------------------------------------------
+// Outer residual r = f(mu) - A(mu) x in FP64 (stored as TR), ||r||^2 and ||f||^2: the
+// march of part B with x in place of p and the load terms read at the thread's points.
+
+template <typename TR, bool FIELD>
+__global__ void __launch_bounds__(zmax_consumers<double>() + 32) k3z_outer(Params P, ZPlan z,
+                                                                            const __grid_constant__ ZMaps maps) {
+    using T = double;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ T mus[MAX_MU];
+    __shared__ double red[32];
+    const Geo& g = P.g;
+    const int mx = g.mx;
+    T* ring = reinterpret_cast<T*>(smem_raw + ZLEAD);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + ZLEAD + (z.ring_elems + z.rbuf_elems) * sizeof(T));
+    const bool producer = (int)threadIdx.x >= z.nthr;
+    const bool issuer = producer && (int)threadIdx.x == z.nthr;
+    int tx = 0, tr = 0;
+    if (!producer) zmap(z, threadIdx.x, tx, tr);
+    const int x0 = 4 * tx;
+    const bool col_ok = !producer && x0 < mx;
+    zsetup<T>(z, ring, bar);
+
+    const int cnt = P.lcnt[L_OUT];
+    const int zc = zchunk(g, z, cnt, P.max_tiles);
+    const int nchunk = (g.mz + zc - 1) / zc;
+    const int per_q = z.ntile_y * nchunk;
+    const long long total = (long long)cnt * per_q;
+    const size_t plane = (size_t)mx * g.my;
+    const uint32_t tbytes_a = (uint32_t)(z.a_rows * mx * sizeof(T));
+
+    // ---- producer (one lane): one tensor copy of x per stage
+    long long pw = blockIdx.x;
+    int pz = 0, pz1 = 0, py0 = 0, pq = 0;
+    unsigned issued = 0, pslot = 0;
+    auto cursor_item = [&](long long w) {
+        for (; w < total; w += gridDim.x) {
+            const int slot = (int)(w / per_q), rem = (int)(w % per_q);
+            const int q = P.lidx[L_OUT * P.Bmax + slot];
+            if (P.st[q].phase == PH_DONE) continue;
+            const int chunk = rem / z.ntile_y, yt = rem % z.ntile_y;
+            py0 = yt * z.ty;
+            const int pz0 = chunk * zc;
+            pz1 = min(g.mz, pz0 + zc);
+            pz = pz0 - 2;
+            pq = q;
+            break;
+        }
+        pw = w;
+    };
+    auto issue_next = [&]() {
+        if (pw >= total) return;
+        ++issued;
+        T* st = ring + (size_t)pslot * z.stage_elems;
+        uint64_t* b = bar + pslot;
+        if (++pslot == (unsigned)z.ring) pslot = 0;
+        mb_arrive_tx(b, tbytes_a);
+        tma4d(st + z.off_a, &maps.a, b, py0 - 1, pz + 1, pq);
+        if (++pz > pz1 - 1) cursor_item(pw + gridDim.x);
+    };
+    if (issuer) {
+        cursor_item(blockIdx.x);
+        for (int i = 0; i < z.ring; ++i) issue_next();
+    }
+
+    unsigned seq = 0, cs = 0, cph = 0;
+    bool ok = true;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        const int slot = (int)(w / per_q), rem = (int)(w % per_q);
+        const int q = P.lidx[L_OUT * P.Bmax + slot];
+        if (P.st[q].phase == PH_DONE) continue;   // uniform across the CTA
+        const int chunk = rem / z.ntile_y, yt = rem % z.ntile_y;
+        const int y0 = yt * z.ty, z0 = chunk * zc, z1 = min(g.mz, z0 + zc);
+        const int y = y0 + tr;
+        const bool row_ok = col_ok && y < g.my;
+        TR* rg = reinterpret_cast<TR*>(P.r) + (size_t)q * g.n;
+        __syncthreads();
+        for (int j = threadIdx.x; j < P.n_mu; j += blockDim.x) mus[j] = P.mu[(size_t)q * P.n_mu + j];
+        __syncthreads();
+        double phi[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) phi[r] = (r < P.R) ? (P.load_param[r] < 0 ? 1.0 : mus[P.load_param[r]]) : 0.0;
+        V4t<T> vm = zero4<T>(), vc = zero4<T>(), vp = zero4<T>();
+        ZCoef<T> c;
+        int ckey = -2;
+        double rr = 0.0, ff = 0.0;
+        const uint32_t own = (uint32_t)((tr + 1) * mx + x0);
+        for (int k = z0 - 2; k <= z1 - 1; ++k) {
+            if (!producer) {
+                const T* sg = ring + (size_t)cs * z.stage_elems;
+                const T* sp = ring + (size_t)(cs == 0 ? z.ring - 1 : cs - 1) * z.stage_elems;   // stage k-1
+                if (ok && !mb_wait(bar + cs, cph, P.err, P.wait_ns)) ok = false;
+                if (col_ok) {
+                    const V4t<T> a = lds4(sg + z.off_a + own);
+                    vm = vc;
+                    vc = vp;
+                    vp = a;
+                    if (k >= z0 && row_ok) {
+                        if constexpr (FIELD) {
+                            zcoef_field<T>(g, query_kappa<T>(g, q), x0, y, k, c);
+                        } else {
+                            const int kk = zkey(g, k);
+                            if (kk != ckey) {
+                                zcoef<T>(g, mus, x0, y, k, c);
+                                ckey = kk;
+                            }
+                        }
+                        const T* ra = sp + z.off_a + own;
+                        const V4t<T> yu = lds4(ra - mx), yd = lds4(ra + mx);
+                        const T left = x0 > 0 ? ra[-1] : T(0), right = x0 + 4 < mx ? ra[4] : T(0);
+                        const size_t gi = (size_t)k * plane + (size_t)y * mx + x0;
+                        // f(mu) at the 4 points (same summation order as the generic kernel)
+                        double f[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            if (r >= P.R) break;
+                            const V4t<double> fr = ldg4(P.fr + (size_t)r * g.n + gi);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) f[j] += phi[r] * fr.v[j];
+                        }
+                        V4t<TR> o;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const double rv = f[j] - zapply(c, j, vm, vc, vp, yu, yd, left, right);
+                            o.v[j] = (TR)rv;
+                            rr += rv * rv;
+                            ff += f[j] * f[j];
+                        }
+                        stg4(rg + gi, o);
+                    }
+                }
+            }
+            __syncthreads();
+            if (issuer && seq >= 1) issue_next();
+            ++seq;
+            if (++cs == (unsigned)z.ring) {
+                cs = 0;
+                cph ^= 1u;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (issuer) zdrain(bar, issued, (unsigned)z.ring, P.wait_ns);
+            __syncthreads();
+            return;
+        }
+        double v[2];
+        cta_sum2(rr, ff, red, v);
+        if (arrive(P, q, rem, per_q, v, 2)) {
+            double tot[2];
+            gather_partials(P, q, per_q, 2, tot, red);
+            if (threadIdx.x == 0) {
+                finalize_outer_state(P, q, tot[0], tot[1]);
+                P.tick[q] = 0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Smoother: one red-black sweep from src to dst (LAST: dst = y, r^T y and
 // (A p)^T y accumulated and the preconditioner finalised).
 
@@ -818,6 +981,12 @@ bool zencode(CUtensorMap* m, const void* base, const Geo& g, long long nq, int r
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool outer_fits(const Geo& g) {
+    const ZPlan z = zplan<double>(g, false, false, true);
+    return z.bytes <= zsmem_cap<double>() && z.nthr <= zmax_consumers<double>() &&
+           (long long)z.ntile_y <= tiles_flat(g.n) && z.a_rows <= 256;
+}
+
 template <typename T>
 bool ztile_fits(const Geo& g) {
     for (int kind = 0; kind < 4; ++kind) {
@@ -838,6 +1007,13 @@ bool use_ztile(const Geo& g, bool fp64) {
     if (g.n >= (1LL << 31) || !zencode_fn()) return false;
     return fp64 ? ztile_fits<double>(g) : ztile_fits<float>(g);
 }
+
+bool use_ztile_outer(const Geo& g) {
+    if (g.dim != 3 || g.mx % 4 != 0 || g.mx > ZMAX_MX || g.mx < 8 || g.my < 2) return false;
+    if (g.n >= (1LL << 31) || !zencode_fn() || (g.nf > 0 && !g.kap64)) return false;
+    return outer_fits(g);
+}
+
 
 // FIELD: coefficient fields (kappa(mu) read per row and plane) instead of block coefficients
 template <typename T, bool FIELD>
@@ -883,6 +1059,18 @@ void smooth_tile_launch(const Params& P, const Launch& L, const ZPlan& zl, const
     }
 }
 
+template <typename TR, bool FIELD>
+void outer_tile_launch(const Params& P, const Launch& L, const ZPlan& z, const ZMaps& maps) {
+    const int threads = z.nthr + 32;
+    static size_t conf = 0;
+    static int grid = 0;
+    if (conf != z.bytes) {
+        grid = zgrid(k3z_outer<TR, FIELD>, threads, z.bytes);
+        conf = z.bytes;
+    }
+    k3z_outer<TR, FIELD><<<grid, threads, z.bytes, L.s>>>(P, z, maps);
+}
+
 template <typename T>
 bool launch3d_cg_tile(const Params& P, const Launch& L, bool part_a) {
     const ZPlan z = zplan<T>(P.g, false, part_a);
@@ -924,5 +1112,21 @@ bool launch3d_smooth_tile(const Params& P, const Launch& L, int nu) {
 }
 template bool launch3d_smooth_tile<float>(const Params&, const Launch&, int);
 template bool launch3d_smooth_tile<double>(const Params&, const Launch&, int);
+
+
+// FP64 outer residual on the tiles; r stored as TR (FP32 for the mixed solver)
+template <typename TR>
+bool launch3d_outer_tile(const Params& P, const Launch& L) {
+    const ZPlan z = zplan<double>(P.g, false, false, true);
+    ZMaps maps;
+    if (!zencode<double>(&maps.a, P.x64, P.g, P.B, z.a_rows)) return false;
+    maps.b = maps.a;
+    maps.c = maps.a;
+    if (P.g.nf > 0) outer_tile_launch<TR, true>(P, L, z, maps);
+    else outer_tile_launch<TR, false>(P, L, z, maps);
+    return true;
+}
+template bool launch3d_outer_tile<float>(const Params&, const Launch&);
+template bool launch3d_outer_tile<double>(const Params&, const Launch&);
 
 }  // namespace rbk
