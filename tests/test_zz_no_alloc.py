@@ -86,7 +86,7 @@ def test_noalloc_rejects_oversized_batches_and_host_memory():
     # a Gaussian load with sigma = 0 is rejected before any device work (it would give 0 / 0)
     w = wl.small((16, 12), (2, 2), n_basis=1, bumps=True)
     p, keep = rb.make_problem(w.problem)
-    keep[1].sigma = 0.0
+    p.loads[1].sigma = 0.0
     mu1 = np.ascontiguousarray(w.test_mu(1))
     xd = torch.zeros((1, w.problem.n_dof), dtype=torch.float64, device="cuda")
     out = np.zeros(1)
