@@ -1369,9 +1369,11 @@ rb_status rb_autotune(rb_ctx* ctx, int B, const double* mu, double* x, rb_opts* 
                 if (kk == base.kernels || (kk == 1 && ctx->geo.dim == 2 && !use_fused_smoother(ctx->geo, base.nu)))
                     continue;
                 if (kk >= 3 && (ctx->geo.dim != 2 || !use_multi_smoother(ctx->geo))) continue;
-                if (kk != 0 && base.store == RB_STORE_BF16) continue;   // BF16 iterates need kernels = 0
                 rb_opts t = base;
                 t.kernels = kk;
+                // BF16 iterates need kernels = 0: the other families are tried with FP32 storage (a
+                // local optimum of the storage must not hide them)
+                if (kk != 0 && t.store == RB_STORE_BF16) t.store = RB_STORE_F32;
                 const double ms = trial(t);
                 if (ms < best_ms) { best_ms = ms; best = t; }
             }
