@@ -69,7 +69,13 @@ BF16_SMOOTH_LAST, BF16_SMOOTH_SWEEP, BF16_PROLONG = 14, 8, 2
 # kernel's source files hash to what they were when the counters were taken (otherwise the line
 # reports traffic null).  Key: (inner precision, storage, kernel family, kernel, nu).  Filled from a
 # capture of the current kernels.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("f32", "f32", 3, "smooth", 9): {
+        "bytes_per_point": 37.1, "sources": ["rb_smooth_multi.cu", "rb_stage.cuh", "rb_common.cuh"],
+        "sha": "6f1320120c1c78ae",
+        "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one application (two passes of "
+                   "k2_smooth_multi<3, 0, 512> and one of <3, 1, 512>), 512x512, 64 queries, nu = 9"},
+}
 
 
 def parse(argv=None):
