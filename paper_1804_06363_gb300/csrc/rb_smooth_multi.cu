@@ -39,6 +39,7 @@ using namespace stg;
 namespace {
 
 constexpr int MS_MAX_NF = 3;
+struct Par2 { static constexpr int value = 2; };   // step tag: uniform key, every row inside
 // Steps of one band: its rows plus 2 NH.  A band has at most TB_ROWS rows, since the
 // partial-sum slots (at least one per TILE points) outnumber the bands of 128-point rows.
 constexpr int MS_MAX_STEPS = TB_ROWS + 2 * 2 * MS_MAX_NF;
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(ms_threads<MX>(), ms_min_blocks<MX, LAST>()) k
         auto step = [&](auto par_tag, auto uni_tag, int k, int kkey) {
             constexpr int PAR = decltype(par_tag)::value;
             constexpr bool UNI = decltype(uni_tag)::value != 0;
+            constexpr bool FULL = decltype(uni_tag)::value == 2;   // every half-sweep's row is inside
             constexpr int J0 = PAR, J1 = PAR + 2;          // updated columns
             constexpr int K0 = 1 - PAR, K1 = 3 - PAR;      // the other colour's columns
             if (ok && !mb_wait(full + cslot, cpar, P.err, P.wait_ns)) ok = false;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(ms_threads<MX>(), ms_min_blocks<MX, LAST>()) k
                 hc[0][0] = hp[0][0];
                 hc[0][1] = hp[0][1];
                 float n0 = 0.f, n1 = 0.f;
-                if (k >= y0 - NH + 1 && k >= 0 && k < my) {
+                if (FULL || (k >= y0 - NH + 1 && k >= 0 && k < my)) {
                     MsCoef c;
                     if constexpr (UNI) {
                         c = ms_pick<J0>(cf);
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(ms_threads<MX>(), ms_min_blocks<MX, LAST>()) k
                 hc[h][0] = hp[h][0];
                 hc[h][1] = hp[h][1];
                 float n0 = 0.f, n1 = 0.f;
-                if (r >= y0 - (NH - 1 - h) && r >= 0 && r < my) {
+                if (FULL || (r >= y0 - (NH - 1 - h) && r >= 0 && r < my)) {
                     MsCoef c;
                     if constexpr (UNI) {
                         c = ms_pick<J0>(cf);
@@ -374,13 +376,17 @@ __global__ void __launch_bounds__(ms_threads<MX>(), ms_min_blocks<MX, LAST>()) k
             }
         };
         for (int k = kfirst; k <= klast; k += 2) {
-            // rows k .. k-NH+1 (clamped to the grid) share a key: uniform over the CTA
+            // u >= 0: rows k .. k-NH+1 (clamped to the grid) share a key, uniform over the CTA; when
+            // they are also all inside the band's trapezoid and the grid (most steps) the step
+            // skips its row tests
             const int u0 = ukey[k - kfirst];
-            if (u0 >= 0) step(Par1{}, Par1{}, k, u0);
+            if (u0 >= 0 && k >= y0 + NH - 1 && k < my) step(Par1{}, Par2{}, k, u0);
+            else if (u0 >= 0) step(Par1{}, Par1{}, k, u0);
             else step(Par1{}, Par0{}, k, u0);
             if (k + 1 <= klast) {
                 const int u1 = ukey[k + 1 - kfirst];
-                if (u1 >= 0) step(Par0{}, Par1{}, k + 1, u1);
+                if (u1 >= 0 && k + 1 >= y0 + NH - 1 && k + 1 < my) step(Par0{}, Par2{}, k + 1, u1);
+                else if (u1 >= 0) step(Par0{}, Par1{}, k + 1, u1);
                 else step(Par0{}, Par0{}, k + 1, u1);
             }
         }
