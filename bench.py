@@ -71,8 +71,8 @@ BF16_SMOOTH_LAST, BF16_SMOOTH_SWEEP, BF16_PROLONG = 14, 8, 2
 # capture of the current kernels.
 NCU_TRAFFIC = {
     ("f32", "f32", 3, "smooth", 9): {
-        "bytes_per_point": 37.1, "sources": ["rb_smooth_multi.cu", "rb_stage.cuh", "rb_common.cuh"],
-        "sha": "6f1320120c1c78ae",
+        "bytes_per_point": 37.56, "sources": ["rb_smooth_multi.cu", "rb_stage.cuh", "rb_common.cuh"],
+        "sha": "4d6d87647bc00ade",
         "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one application (two passes of "
                    "k2_smooth_multi<3, 0, 512> and one of <3, 1, 512>), 512x512, 64 queries, nu = 9"},
 }
