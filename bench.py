@@ -93,9 +93,10 @@ def parse(argv=None):
     ap.add_argument("--fp64-queries", type=int, default=0,
                     help="queries of the FP64 plain comparator (default: the timed batch; -1: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-nu", type=int, default=6,
+    ap.add_argument("--cpu-nu", type=int, default=9,
                     help="reference arm: smoother sweeps of the oracle (the GPU arm's tuned value on the default "
-                         "workload); the GPU arm's own CPU baseline uses its tuned value")
+                         "workload; stored oracle counts exist for 1, 6 and 9); the GPU arm's own CPU baseline "
+                         "uses its tuned value")
     ap.add_argument("--cpu-iters", type=int, default=60,
                     help="reference arm: Alg. 3 iterations per core and step (about 10 s of oracle work)")
     ap.add_argument("--basis", default="", help="basis file: loaded if it exists, else built and saved there")

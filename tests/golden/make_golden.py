@@ -13,7 +13,11 @@ Contents, for the 512 x 512, 3 x 3-block, two-bump workload with n = 40:
   * `*_half`: the same solves when a restarted cycle aims at half the
     tolerance (restart_factor 0.5), the CUDA library's FP64 restart policy,
     for comparing its iteration counts.
-It calls only `oracle/` and `workloads`.  Run: python tests/golden/make_golden.py
+  * `iters_nu9`, `rel_res_nu9`, `restarts_nu9`: the plain-rule solves with nine sweeps (the
+    autotuner's choice once the smoother runs three sweeps per pass), added to an existing file by
+    `--add-nu 9` with the basis rebuilt from `selected` (the reference arm of bench.py scales its
+    iteration rate by these counts).
+It calls only `oracle/` and `workloads`.  Run: python tests/golden/make_golden.py [--add-nu NU]
 """
 from __future__ import annotations
 
@@ -87,5 +91,31 @@ def main():
     print(json.dumps(out))
 
 
+def add_nu(nu: int):
+    """Add the plain-rule solves with `nu` sweeps to the stored file (basis from its selection)."""
+    _worker_init()
+    import workloads as wl
+    from oracle import baseline
+    with open(OUT) as f:
+        out = json.load(f)
+    w = wl.rbcg_2d_512()
+    assert out["workload"] == w.name
+    mu = w.test_mu(N_TEST)
+    pool = baseline.pool(min(N_TEST, os.cpu_count() or 1))
+    basis = baseline.basis_from_selection("rbcg_2d_512", out["selected"], pool)
+    res = pool.map(_solve, [(basis.W, basis.ANq, basis.fNr, mu[i], "pr", nu, 1.0) for i in range(N_TEST)])
+    pool.close()
+    out[f"iters_nu{nu}"] = [int(r[0]) for r in res]
+    out[f"rel_res_nu{nu}"] = [float(r[1]) for r in res]
+    out[f"restarts_nu{nu}"] = [int(r[3]) for r in res]
+    out["source"] += f"; nu={nu} added from the stored selection"
+    with open(OUT, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({k: out[k] for k in (f"iters_nu{nu}", f"restarts_nu{nu}")}))
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) == 3 and sys.argv[1] == "--add-nu":
+        add_nu(int(sys.argv[2]))
+    else:
+        main()
