@@ -336,7 +336,7 @@ rb_status rb_warm_start(rb_ctx* ctx, rb_mlp* net, int B, const double* mu, doubl
  * gain leaves span(W): x_0 = x_hat(mu) + V z(mu), with x_hat = W a_N(mu) the RB
  * approximation of eq. 3 and V an orthonormal basis of the errors
  * e_s = x_s - x_hat(mu_s) of training solutions (the paper has no learned
- * component; this is the benchmark spec's learned warm start).
+ * component; this is an addition to its method).
  *
  * rb_error_basis: proper orthogonal decomposition of the errors of S training
  * solutions by the method of snapshots (Gram matrix E^T E in FP64 on the
