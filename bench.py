@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -243,6 +244,23 @@ def tune(ctx, w, x, opts, n_sample: int = TUNE_SAMPLE):
     return tuned
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: implementer and part codes)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = (t.strip() for t in line.split(":", 1))
+            fields.setdefault(k, v)
+    if "model name" in fields:
+        return fields["model name"]
+    parts = [f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part") if k in fields]
+    return " ".join([platform.machine()] + parts) if parts else platform.machine()
+
+
 def parity_sample(B: int, k: int):
     """Seeded sample of k query indices of a batch of B (sorted)."""
     import numpy as np
@@ -304,7 +322,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": w.name, "solver": "oracle FP64 Alg. 3 (numpy)",
                                             "smoother": f"red-black GS nu={args.cpu_nu}", "beta": "pr",
                                             "tol": 1e-10, "cores": cores},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -814,7 +832,7 @@ def main():
             idx = parity_sample(B, cores)
             wall, out = runner.solve([mu[i] for i in idx], opts["nu"])
             its = [o[0] for o in out]
-            cpu = {"value": len(idx) / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            cpu = {"value": len(idx) / wall, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                    "sample": (f"{len(idx)} complete solves of seeded test queries of the timed batch, one per core, "
                               f"oracle FP64 Alg. 3 with the GPU arm's {opts['nu']} red-black sweeps, PR beta, "
                               f"tol 1e-10 ({wall:.1f} s wall, {np.mean(its):.1f} iterations per solve)"),
