@@ -206,3 +206,21 @@ def test_rbcg_on_the_cases_reaches_the_truth_and_beats_cg(case):
         assert np.linalg.norm(res.x - truth) <= 1e-8 * np.linalg.norm(truth)
         _, plain_iters, _ = direct.cg(prob, mu, tol=1e-10)
         assert res.iters * 2 <= plain_iters, (res.iters, plain_iters)
+
+
+def test_parameter_streams_are_distinct_and_in_the_paper_domains():
+    """The training, test and autotuner streams of a case are disjoint draws from the paper's
+    domains ([0, 1] for Case 1, [0, 2] x [0, 1] for Case 2), and the affine coefficients follow
+    the case's map: theta_0 = 1 and, for Case 2, phi = (1 - mu_2, mu_1 (1 - mu_2), mu_2, mu_1 mu_2)."""
+    for case, dom in (("case1", [(0.0, 1.0)]), ("case2", [(0.0, 2.0), (0.0, 1.0)])):
+        w = wl.paper_case(case, 8)
+        train, test, tune = w.train_mu(), w.test_mu(), wl.tune_mu(w, 64)
+        for a, b in ((train, test), (train, tune), (test, tune)):
+            assert not np.any(np.all(np.isclose(a[:, None, :], b[None, :, :]), axis=2))
+        phys = w.draw_physical(w.train_seed, w.n_train)
+        for d, (lo, hi) in enumerate(dom):
+            assert np.all((phys[:, d] >= lo) & (phys[:, d] < hi))
+        assert np.all(train[:, 0] == 1.0)
+        if case == "case2":
+            m1, m2 = phys[:, 0], phys[:, 1]
+            np.testing.assert_allclose(train[:, 1:], np.stack([m1, 1 - m2, m1 * (1 - m2), m2, m1 * m2], axis=1))
