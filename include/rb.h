@@ -80,8 +80,10 @@ typedef struct {
     int n_mu;           /* entries of one parameter vector (>= P and > every load param) */
     int n_fields;       /* 0: block coefficients; Q >= 1: coefficient fields, P = Q */
     const double* fields;   /* [Q][N_dof] node values F_q (host, copied when a context is created;
-                               NULL when n_fields = 0).  Field problems run the generic stencil
-                               kernels (rb_opts.kernels is ignored). */
+                               NULL when n_fields = 0).  On 3D grids whose rows hold a
+                               multiple of 4 points field problems run the z-march tile kernels
+                               (rb_opts.kernels = 0; they read kappa(mu) at the nodes), elsewhere
+                               the generic stencil kernels. */
 } rb_problem;
 
 enum { RB_SMOOTH_NONE = 0, RB_SMOOTH_RBGS = 1, RB_SMOOTH_JACOBI = 2 };
