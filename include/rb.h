@@ -120,10 +120,11 @@ typedef struct {
                            3: as 0, but up to three red-black sweeps per pass over memory (FP32
                               mixed path with FP32 storage; other cases as 0);
                            4: as 3 with up to two sweeps per pass.
-                           On 3D grids (RBCG): 0 marches the CG body and the red-black smoother in
-                           z with planes prefetched into shared memory by asynchronous copies;
-                           1 the smoother marching in z with direct loads and the generic CG
-                           body; 2 the generic kernels.  Other grids take the generic kernels. */
+                           On 3D grids (RBCG): 0 marches the CG body, the red-black smoother and
+                           the FP64 outer residual in z with planes prefetched into shared memory
+                           by asynchronous tensor copies; 1 the smoother marching in z with direct
+                           loads and the generic CG body (block coefficients only); 2 the generic
+                           kernels.  Other grids take the generic kernels. */
     int store;          /* RB_STORE_*: storage of the preconditioner's intermediate vectors (the
                            prolongation W e_N and the smoother sweeps before the last one).
                            RB_STORE_BF16 halves their bytes; the arithmetic stays FP32 and the
